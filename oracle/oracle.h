@@ -1,0 +1,164 @@
+/*
+ * CPU FP64 oracle for the single-GPU short-range MD hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant generator with the CUDA path.
+ *
+ * Every function is a plain, slow, obviously correct statement of what the
+ * method computes (Glaser et al., "Strong scaling of general-purpose molecular
+ * dynamics simulations on GPUs"):
+ *   - periodic box with the minimum-image convention (Sec. 4.1),
+ *   - Verlet neighbour list of radius r_cut + r_buff, rebuilt when a particle
+ *     moved more than half the buffer length (Sec. 4.2),
+ *   - cell-list binning (Sec. 4.3.3) and the per-particle neighbour rows of
+ *     the cooperative-thread-array algorithm (Sec. 5.1, Fig. "nlist"),
+ *   - LJ 12-6 and DPD pair forces, DPD random numbers seeded with global
+ *     particle IDs (Sec. 3, Sec. 9),
+ *   - harmonic bonds between an unordered pair of particle IDs (Sec. 4.3.4),
+ *   - velocity-Verlet NVE / DPD integration (Sec. 3),
+ *   - grouped thermodynamic reductions (Sec. 4.3.3).
+ *
+ * Layouts: positions / velocities / forces are double[N][4]; force w holds the
+ * per-particle potential energy.  Image counters are int32[N][4].  Virials are
+ * double[N][6] (xx, xy, xz, yy, yz, zz).  Pair coefficients are per ordered
+ * type pair: coeff[2 * (ti * ntypes + tj) + {0,1}] = (eps, sigma) for LJ and
+ * (A, gamma) for DPD.
+ *
+ * Floating-point contract: compiled with -ffp-contract=off, so every product
+ * and sum is rounded separately, in source order.
+ */
+#ifndef MD_ORACLE_H
+#define MD_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Number of cells per box edge for a cell list of minimum width r_list:
+ * floor(L / r_list), capped at 512.  Returns 0 when fewer than 3 fit. */
+int32_t orc_cells_per_dim(double L, double r_list);
+
+/* Integer cell coordinates of every particle, cell[i][d] in [0, nc[d]). */
+void orc_cell_coords(int64_t n, const double *pos, const double *L,
+                     const int32_t *nc, int32_t *cell);
+
+/* Full neighbour rows by brute force: j != i with r^2 < r_list^2 (strict).
+ * rows[i * max_nb + k] in ascending j.  Returns the largest row length
+ * (rows longer than max_nb are truncated but counted). */
+int32_t orc_neighbors_brute(int64_t n, const double *pos, const double *L,
+                            double r_list, int32_t *counts, int32_t *rows,
+                            int32_t max_nb);
+
+/* The same neighbour rows through a cell list (O(N)); boxes with fewer than
+ * 3 cells per edge use the all-pairs loop. */
+int32_t orc_neighbors_cells(int64_t n, const double *pos, const double *L,
+                            double r_list, int32_t *counts, int32_t *rows,
+                            int32_t max_nb);
+
+/* LJ 12-6 pair: returns force magnitude divided by r, writes V(r). */
+double orc_lj_pair(double r2, double eps, double sigma, double *v);
+
+/* LJ forces over all pairs within r_cut.  force[i] = (F_i, PE_i); PE_i is half
+ * the sum of the pair energies (shifted by V(r_cut) when shift_energy != 0).
+ * virial and absf (sum over j of |f_ij|) may be NULL. */
+void orc_lj_forces_brute(int64_t n, const double *pos, const int32_t *type,
+                         const double *L, double r_cut, int32_t ntypes,
+                         const double *coeff, int32_t shift_energy,
+                         double *force, double *virial, double *absf);
+
+/* LJ forces from full neighbour rows (as written by orc_neighbors_*). */
+void orc_lj_forces_nlist(int64_t n, const double *pos, const int32_t *type,
+                         const double *L, double r_cut, int32_t ntypes,
+                         const double *coeff, int32_t shift_energy,
+                         const int32_t *counts, const int32_t *rows,
+                         int32_t max_nb, double *force, double *virial,
+                         double *absf);
+
+/* Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11). */
+void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out);
+
+/* DPD pair noise theta_ij = sqrt(3) (2u - 1), u = (w0 + 1/2) 2^-32, where w0
+ * is word 0 of Philox-4x32-10 with counter (min tag, max tag, step lo,
+ * step hi) and key (seed lo, seed hi).  Symmetric in (tag_i, tag_j). */
+double orc_dpd_theta(int32_t tag_i, int32_t tag_j, uint64_t step, uint64_t seed);
+
+/* DPD (Groot-Warren) forces over all pairs within r_cut. */
+void orc_dpd_forces_brute(int64_t n, const double *pos, const double *vel,
+                          const int32_t *type, const int32_t *tag,
+                          const double *L, double r_cut, int32_t ntypes,
+                          const double *coeff, double kT, double dt,
+                          uint64_t step, uint64_t seed, double *force,
+                          double *virial, double *absf);
+
+/* DPD forces from full neighbour rows. */
+void orc_dpd_forces_nlist(int64_t n, const double *pos, const double *vel,
+                          const int32_t *type, const int32_t *tag,
+                          const double *L, double r_cut, int32_t ntypes,
+                          const double *coeff, double kT, double dt,
+                          uint64_t step, uint64_t seed, const int32_t *counts,
+                          const int32_t *rows, int32_t max_nb, double *force,
+                          double *virial, double *absf);
+
+/* Harmonic bonds V = K/2 (r - r0)^2 between particle indices bonds[2b],
+ * bonds[2b+1].  ADDS to force (and PE in force w, half per end), virial, absf
+ * (any of virial / absf may be NULL). */
+void orc_bond_forces(int64_t n_bonds, const int32_t *bonds, const double *pos,
+                     const double *L, double K, double r0, double *force,
+                     double *virial, double *absf);
+
+/* Velocity Verlet, first half: v += dt/2 F/m; x += dt v; wrap into [0, L)
+ * and count the crossings in image. */
+void orc_vv_first(int64_t n, double *pos, double *vel, int32_t *image,
+                  const double *force, double dt, double mass, const double *L);
+
+/* Velocity Verlet, second half: v += dt/2 F/m. */
+void orc_vv_second(int64_t n, double *vel, const double *force, double dt,
+                   double mass);
+
+/* out = {KE, PE, W, P, T, px, py, pz}: kinetic and potential energy, virial
+ * trace W, pressure (2 KE + W) / (3 V), temperature 2 KE / (3N - 3), momentum.
+ * virial may be NULL (then W = P's virial part = 0). */
+void orc_thermo(int64_t n, const double *vel, const double *force,
+                const double *virial, double mass, const double *L, double *out);
+
+/* 3-D Hilbert index of a cell of a 2^bits grid (Skilling, AIP Conf. Proc. 707,
+ * 2004: axes-to-transpose, then bit interleave). */
+uint64_t orc_hilbert3(uint32_t x, uint32_t y, uint32_t z, int32_t bits);
+
+/* Space-filling-curve order: particles ordered by the Hilbert index of their
+ * cell (cell list of minimum width r_list), ties by index. */
+void orc_sfc_order(int64_t n, const double *pos, const double *L, double r_list,
+                   int32_t *order);
+
+typedef struct {
+    double L[3];
+    double r_cut, r_skin, dt, mass, kT;
+    uint64_t seed;
+    int32_t pair;          /* 0 = LJ, 1 = DPD */
+    int32_t ntypes;
+    const double *coeff;
+    int32_t shift_energy;
+    int32_t thermo_period; /* 0 = never */
+    double K, r0;          /* harmonic bonds */
+    int64_t n_bonds;
+    const int32_t *bonds;  /* index pairs */
+    int64_t step0;         /* time step of the initial state */
+    int32_t max_nb;
+} orc_params;
+
+/* Whole MD loop: forces at step0, then n_steps velocity-Verlet steps with a
+ * Verlet list rebuilt when any particle moved more than r_skin/2 since the
+ * last build.  thermo_out receives 8 doubles (orc_thermo) at every step t
+ * with t % thermo_period == 0, t > step0.  force holds the final forces.
+ * Returns the number of neighbour-list builds, or -1 on row overflow. */
+int64_t orc_run(int64_t n, double *pos, double *vel, int32_t *image,
+                const int32_t *type, const int32_t *tag, double *force,
+                const orc_params *p, int64_t n_steps, double *thermo_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

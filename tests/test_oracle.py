@@ -1,0 +1,396 @@
+"""Pins for the CPU FP64 oracle (no GPU).
+
+Each test checks the oracle against something other than itself: published
+known-answer values, closed forms, lattice symmetry, crystallographic shell
+counts, conservation laws, brute force on small inputs, or the mathematics of
+the integrator.  A plausible slip in the oracle (dropped term, wrong sign,
+wrong index, transposed operand) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_3387_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# --------------------------------------------------------------------------
+# LJ pair
+
+def test_lj_special_values():
+    vals = {"1": 1.0, "2^(1/6)": 2.0 ** (1.0 / 6.0)}
+    for q, r, v in _golden_rows("lj_special_values.txt"):
+        fr, pot = oracle.lj_pair(vals[r] ** 2)
+        got = pot if q == "V" else fr * vals[r]
+        assert got == pytest.approx(float(v), abs=1e-13)
+
+
+def test_lj_scaling_with_eps_and_sigma():
+    # V(r; eps, s) = eps V(r/s; 1, 1) and F(r; eps, s) = eps/s F(r/s; 1, 1)
+    for eps, s, x in [(2.0, 1.5, 1.1), (0.5, 0.8, 1.7), (3.0, 1.0, 2.4)]:
+        fr1, v1 = oracle.lj_pair(x * x)
+        frs, vs = oracle.lj_pair((x * s) ** 2, eps, s)
+        assert vs == pytest.approx(eps * v1, rel=1e-14)
+        assert frs * (x * s) == pytest.approx(eps / s * fr1 * x, rel=1e-14)
+
+
+def test_lj_two_particles_direction_and_image():
+    # particle 1 at distance 1 from particle 0 across the periodic boundary
+    L = 10.0
+    pos = np.zeros((2, 4))
+    pos[0, :3] = [0.3, 5.0, 5.0]
+    pos[1, :3] = [L - 0.7, 5.0, 5.0]  # separation x0 - x1 = +1 (minimum image)
+    f, vir, absf = oracle.lj_forces(pos, L, 2.5)
+    # at r = sigma the pair force has magnitude 24 and is repulsive
+    assert f[0, 0] == pytest.approx(24.0, abs=1e-12)
+    assert f[1, 0] == pytest.approx(-24.0, abs=1e-12)
+    assert np.allclose(f[:, 1:3], 0.0)
+    assert f[0, 3] == pytest.approx(0.0, abs=1e-14)  # V(sigma) = 0, half each
+    # virial: half of r f per particle (x0 - x1 = +1, f_x = +24)
+    assert vir[0, 0] == pytest.approx(12.0, abs=1e-12)
+    assert absf[0] == pytest.approx(24.0, abs=1e-12)
+
+
+def _fcc_shells():
+    return [(int(k), int(z)) for k, z in _golden_rows("fcc_shells.txt")]
+
+
+@pytest.mark.parametrize("rho,r_cut", [(0.8442, 2.5), (1.0, 3.0), (0.7, 2.5)])
+def test_lj_perfect_fcc_lattice_sum(rho, r_cut):
+    st = inputs.lj_fluid(4 * 6 ** 3, rho, 1.0, seed=1)  # perfect 6^3 lattice
+    L = st.box[0, 0]
+    a = L / 6
+    f, vir, absf = oracle.lj_forces(st.pos, L, r_cut)
+    # zero net force on every site by inversion symmetry
+    assert np.max(np.abs(f[:, :3])) <= 1e-12 * np.max(absf)
+    # energy and virial per particle from the crystallographic shells
+    pe, w = 0.0, 0.0
+    for k, z in _fcc_shells():
+        r = a * math.sqrt(k / 2.0)
+        if r >= r_cut:
+            continue
+        fr, v = oracle.lj_pair(r * r)
+        pe += 0.5 * z * v
+        w += 0.5 * z * fr * r * r
+    assert np.allclose(f[:, 3], pe, rtol=1e-12, atol=1e-13)
+    assert np.allclose(vir[:, 0] + vir[:, 3] + vir[:, 5], w, rtol=1e-11, atol=1e-12)
+    # neighbour rows: the number of sites inside r_cut is the shell count sum
+    counts, _ = oracle.neighbors(st.pos, L, r_cut, max_nb=256)
+    z_in = sum(z for k, z in _fcc_shells() if a * math.sqrt(k / 2.0) < r_cut)
+    assert np.all(counts == z_in)
+
+
+def test_lj_newton_third_law_and_shift():
+    st = inputs.lj_fluid(500, 0.8442, 1.0, seed=3, jitter=0.08)
+    L = st.box[0, 0]
+    f, _, absf = oracle.lj_forces(st.pos, L, 2.5)
+    assert np.abs(f[:, :3].sum(0)).max() <= 1e-12 * absf.sum()
+    fs, _, _ = oracle.lj_forces(st.pos, L, 2.5, shift_energy=True)
+    # shifting changes only the energy, by V(r_c) per pair
+    assert np.array_equal(fs[:, :3], f[:, :3])
+    counts, _ = oracle.neighbors(st.pos, L, 2.5)
+    _, vc = oracle.lj_pair(2.5 ** 2)
+    assert np.allclose(fs[:, 3], f[:, 3] - 0.5 * counts * vc, rtol=1e-12, atol=1e-12)
+
+
+def test_lj_multitype_coefficients_index_by_type_pair():
+    st = inputs.lj_fluid(256, 0.8, 1.0, seed=4, jitter=0.1)
+    L = st.box[0, 0]
+    t = np.arange(256) % 2
+    coeff = np.array([[[1.0, 1.0], [0.5, 1.1]], [[0.5, 1.1], [2.0, 0.9]]])
+    f, _, absf = oracle.lj_forces(st.pos, L, 2.5, coeff=coeff, type=t)
+    # brute recomputation from the pair function with per-pair coefficients
+    i = 7
+    acc = np.zeros(3)
+    for j in range(256):
+        if j == i:
+            continue
+        d = st.pos[i, :3] - st.pos[j, :3]
+        d -= L * np.rint(d / L)
+        r2 = d @ d
+        if r2 < 6.25:
+            e, s = coeff[t[i], t[j]]
+            fr, _ = oracle.lj_pair(r2, e, s)
+            acc += fr * d
+    assert np.allclose(f[i, :3], acc, rtol=1e-12, atol=1e-12)
+    assert np.abs(f[:, :3].sum(0)).max() <= 1e-12 * absf.sum()
+
+
+# --------------------------------------------------------------------------
+# neighbour rows and cells
+
+@pytest.mark.parametrize("seed,n,rho,r_list", [(5, 1000, 0.8442, 2.8), (6, 3000, 3.0, 1.3),
+                                                (7, 700, 0.5, 2.9)])
+def test_neighbors_cells_equal_brute_force(seed, n, rho, r_list):
+    st = inputs.lj_fluid(n, rho, 1.0, seed=seed, jitter=0.3)
+    L = st.box[0, 0]
+    cb, rb = oracle.neighbors(st.pos, L, r_list, method="brute")
+    cc, rc = oracle.neighbors(st.pos, L, r_list, method="cells")
+    assert np.array_equal(cb, cc)
+    assert np.array_equal(rb, rc)
+    # symmetric relation
+    pairs = {(i, j) for i in range(n) for j in rb[i, :cb[i]]}
+    assert all((j, i) in pairs for i, j in pairs)
+
+
+def test_neighbors_exact_distance_threshold():
+    # a pair exactly at r_list is excluded (strict), slightly inside included
+    L = 12.0
+    pos = np.zeros((3, 4))
+    pos[0, :3] = [1.0, 1.0, 1.0]
+    pos[1, :3] = [3.5, 1.0, 1.0]           # r = 2.5 exactly
+    pos[2, :3] = [1.0, 1.0, 1.0 + 2.4999]  # inside
+    c, r = oracle.neighbors(pos, L, 2.5, method="brute")
+    assert c.tolist() == [1, 0, 1]
+    assert r[0, 0] == 2
+
+
+def test_cell_coords_bounds_and_counts():
+    st = inputs.dpd_fluid(5000, 3.0, 1.0, seed=8)
+    L = st.box[0, 0]
+    nc = oracle.cells_per_dim(L, 1.3)
+    assert nc == math.floor(L / 1.3)
+    cc = oracle.cell_coords(st.pos, L, [nc] * 3)
+    assert cc.min() >= 0 and cc.max() < nc
+    h = L / nc
+    x = st.pos[:, :3]
+    assert np.all(x >= cc * h - 1e-12) and np.all(x < (cc + 1) * h + 1e-12)
+    assert oracle.cells_per_dim(5.0, 2.0) == 0  # fewer than 3 cells
+
+
+# --------------------------------------------------------------------------
+# Philox and DPD
+
+def test_philox_known_answers():
+    for row in _golden_rows("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in row]
+        out = oracle.philox4x32_10(v[:4], v[4:6])
+        assert out.tolist() == v[6:10]
+
+
+def test_dpd_theta_symmetric_and_unit_variance():
+    rng = np.random.default_rng(0)
+    a = rng.integers(0, 2 ** 31 - 1, 20000)
+    b = rng.integers(0, 2 ** 31 - 1, 20000)
+    th = np.array([oracle.dpd_theta(x, y, 17, 99) for x, y in zip(a, b)])
+    th2 = np.array([oracle.dpd_theta(y, x, 17, 99) for x, y in zip(a, b)])
+    assert np.array_equal(th, th2)
+    assert abs(th.mean()) < 0.03
+    assert abs(th.var() - 1.0) < 0.03
+    assert th.max() < math.sqrt(3) and th.min() > -math.sqrt(3)
+    # the noise changes with the step and the seed
+    assert oracle.dpd_theta(1, 2, 17, 99) != oracle.dpd_theta(1, 2, 18, 99)
+    assert oracle.dpd_theta(1, 2, 17, 99) != oracle.dpd_theta(1, 2, 17, 98)
+
+
+def test_dpd_two_particle_closed_forms():
+    L = 10.0
+    pos = np.zeros((2, 4))
+    vel = np.zeros((2, 4))
+    pos[0, :3] = [5.5, 5.0, 5.0]
+    pos[1, :3] = [5.0, 5.0, 5.0]  # e = +x, r = 0.5, w = 0.5
+    # conservative only: A w = 12.5 repulsive; V = A rc w^2 / 2 = 3.125
+    f, _, _ = oracle.dpd_forces(pos, vel, L, 1.0, [[25.0, 0.0]], kT=0.0, dt=0.02,
+                                step=0, seed=1)
+    assert f[0, 0] == pytest.approx(12.5, abs=1e-13)
+    assert f[1, 0] == pytest.approx(-12.5, abs=1e-13)
+    assert f[0, 3] + f[1, 3] == pytest.approx(3.125, abs=1e-13)
+    # dissipative only: -gamma w^2 (e . v_ij), v_ij = v_0 - v_1 = +1 along e
+    vel[0, 0] = 1.0
+    f, _, _ = oracle.dpd_forces(pos, vel, L, 1.0, [[0.0, 4.5]], kT=0.0, dt=0.02,
+                                step=0, seed=1)
+    assert f[0, 0] == pytest.approx(-4.5 * 0.25, abs=1e-13)
+    # random only (gamma > 0, kT > 0, no relative velocity):
+    # sigma w theta / sqrt(dt), sigma = sqrt(2 gamma kT) = 3
+    vel[:] = 0.0
+    f, _, _ = oracle.dpd_forces(pos, vel, L, 1.0, [[0.0, 4.5]], kT=1.0, dt=0.02,
+                                step=5, seed=1)
+    th = oracle.dpd_theta(0, 1, 5, 1)
+    assert f[0, 0] == pytest.approx(3.0 * 0.5 * th / math.sqrt(0.02), rel=1e-13)
+    assert f[1, 0] == pytest.approx(-f[0, 0], rel=1e-15)
+
+
+def test_dpd_momentum_conservation_and_tag_invariance():
+    st = inputs.dpd_fluid(1500, 3.0, 1.0, seed=9)
+    L = st.box[0, 0]
+    f, _, absf = oracle.dpd_forces(st.pos, st.vel, L, 1.0, [[25.0, 4.5]], 1.0, 0.02,
+                                   step=3, seed=11)
+    assert np.abs(f[:, :3].sum(0)).max() <= 1e-12 * absf.sum()
+    # permuting particles (with their tags) permutes the forces exactly
+    perm = np.random.default_rng(1).permutation(1500)
+    fp, _, _ = oracle.dpd_forces(st.pos[perm], st.vel[perm], L, 1.0, [[25.0, 4.5]], 1.0,
+                                 0.02, step=3, seed=11, tag=st.tag[perm])
+    assert np.allclose(fp, f[perm], rtol=1e-12, atol=1e-12 * absf.max())
+
+
+def test_dpd_nlist_equals_brute():
+    st = inputs.dpd_fluid(2000, 3.0, 1.0, seed=10)
+    L = st.box[0, 0]
+    nl = oracle.neighbors(st.pos, L, 1.3, max_nb=128, method="cells")
+    coeff = [[25.0, 4.5]]
+    fb, vb, _ = oracle.dpd_forces(st.pos, st.vel, L, 1.0, coeff, 1.0, 0.02, 4, 7)
+    fn, vn, _ = oracle.dpd_forces(st.pos, st.vel, L, 1.0, coeff, 1.0, 0.02, 4, 7, nlist=nl)
+    assert np.allclose(fb, fn, rtol=1e-13, atol=1e-12)
+    assert np.allclose(vb, vn, rtol=1e-13, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# bonds and integration
+
+def test_bond_two_bead_closed_form():
+    L = 20.0
+    pos = np.zeros((2, 4))
+    pos[0, :3] = [1.0, 2.0, 3.0]
+    pos[1, :3] = [1.9, 2.0, 3.0]  # r = 0.9 along +x from 0 to 1
+    f, vir, _ = oracle.bond_forces([[0, 1]], pos, L, K=4.0, r0=0.0)
+    assert f[0, 0] == pytest.approx(3.6, abs=1e-13)   # pulled toward 1
+    assert f[1, 0] == pytest.approx(-3.6, abs=1e-13)
+    assert f[0, 3] + f[1, 3] == pytest.approx(0.5 * 4.0 * 0.81, abs=1e-13)
+    f, _, _ = oracle.bond_forces([[0, 1]], pos, L, K=4.0, r0=1.0)
+    # stretched below r0 = 1: pushed apart with K (r0 - r) = 0.4
+    assert f[0, 0] == pytest.approx(-0.4, abs=1e-13)
+
+
+def test_harmonic_dimer_oscillation_period():
+    # a bonded dimer (no pair forces) oscillates with omega = sqrt(2K/m)
+    K, dt = 4.0, 1e-3
+    L = np.array([50.0, 50.0, 50.0])
+    pos = np.zeros((2, 4))
+    vel = np.zeros((2, 4))
+    pos[0, :3] = [25.0, 25.0, 25.0]
+    pos[1, :3] = [25.5, 25.0, 25.0]
+    img = np.zeros((2, 4), np.int32)
+    period = 2 * math.pi / math.sqrt(2 * K)
+    n = int(round(period / dt))
+    f, _, _ = oracle.bond_forces([[0, 1]], pos, L, K, 0.0)
+    for _ in range(n):
+        pos, vel, img = oracle.vv_first(pos, vel, img, f, dt, L)
+        f, _, _ = oracle.bond_forces([[0, 1]], pos, L, K, 0.0)
+        vel = oracle.vv_second(vel, f, dt)
+    sep = pos[1, 0] - pos[0, 0]
+    assert sep == pytest.approx(0.5, abs=2e-3)
+    assert abs(vel[0, 0]) < 0.01
+
+
+def test_vv_first_wraps_and_counts_images():
+    L = np.array([10.0, 10.0, 10.0])
+    pos = np.array([[9.95, 0.02, 5.0, 0.0]])
+    vel = np.array([[10.0, -10.0, 0.0, 0.0]])
+    f = np.zeros((1, 4))
+    img = np.zeros((1, 4), np.int32)
+    p, v, im = oracle.vv_first(pos, vel, img, f, 0.01, L)
+    assert p[0, 0] == pytest.approx(0.05, abs=1e-12) and im[0, 0] == 1
+    assert p[0, 1] == pytest.approx(9.92, abs=1e-12) and im[0, 1] == -1
+    assert np.all(p[0, :3] >= 0) and np.all(p[0, :3] < 10.0)
+
+
+def test_thermo_of_maxwell_boltzmann_input():
+    st = inputs.lj_fluid(4000, 0.8442, 1.44, seed=12)
+    th = oracle.thermo(st.vel, np.zeros((4000, 4)), None, st.box[0])
+    assert th["temperature"] == pytest.approx(1.44, rel=1e-12)
+    assert th["ke"] == pytest.approx(0.5 * (3 * 4000 - 3) * 1.44, rel=1e-12)
+    assert max(abs(th["px"]), abs(th["py"]), abs(th["pz"])) < 1e-10
+    V = st.box[0, 0] ** 3
+    assert th["pressure"] == pytest.approx(2 * th["ke"] / (3 * V), rel=1e-12)
+
+
+def test_time_reversibility_lj():
+    st = inputs.lj_fluid(864, 0.8442, 1.44, seed=13)
+    L = st.box[0]
+    kw = dict(r_cut=2.5, r_skin=0.3, dt=0.005)
+    a = oracle.run(st.pos, st.vel, st.image, L, 60, **kw)
+    b = oracle.run(a["pos"], -a["vel"], a["image"], L, 60, **kw)
+    x0 = st.pos[:, :3] + st.image[:, :3] * L
+    x1 = b["pos"][:, :3] + b["image"][:, :3] * L
+    assert np.max(np.abs(x1 - x0)) < 1e-9
+    assert np.max(np.abs(b["vel"][:, :3] + st.vel[:, :3])) < 1e-9
+    assert a["builds"] > 1  # the list was rebuilt along the way
+
+
+def test_nve_energy_drift_small_lj():
+    # melting fcc start; velocity Verlet conserves the shifted LJ energy up to
+    # the small drift caused by truncating the force at r_cut.  (The 1e-4
+    # eps/particle bound over 1e4 steps is checked at N = 4000 on the GPU;
+    # this short CPU run bounds the drift rate loosely but still catches a
+    # broken half-kick or a wrong energy term by orders of magnitude.)
+    n = 2048
+    st = inputs.lj_fluid(n, 0.8442, 1.44, seed=14)
+    L = st.box[0]
+    eq = oracle.run(st.pos, st.vel, st.image, L, 400, r_cut=2.5, r_skin=0.3, dt=0.005)
+    out = oracle.run(eq["pos"], eq["vel"], eq["image"], L, 2000, r_cut=2.5, r_skin=0.3,
+                     dt=0.005, shift_energy=True, thermo_period=10, step0=400)
+    e = (out["thermo"][:, 0] + out["thermo"][:, 1]) / n
+    t = np.arange(e.size) * 10 * 0.005
+    slope = np.polyfit(t, e, 1)[0]
+    assert abs(slope) * 1e4 * 0.005 < 3e-4
+    assert np.max(np.abs(e - e[0])) < 1e-3
+    # without the energy shift the same trajectory does not conserve "energy"
+    raw = oracle.run(eq["pos"], eq["vel"], eq["image"], L, 200, r_cut=2.5, r_skin=0.3,
+                     dt=0.005, shift_energy=False, thermo_period=10, step0=400)
+    e_raw = (raw["thermo"][:, 0] + raw["thermo"][:, 1]) / n
+    assert np.max(np.abs(e_raw - e_raw[0])) > np.max(np.abs(e[:20] - e[0]))
+
+
+def test_run_nlist_forces_equal_brute_force_after_steps():
+    st = inputs.lj_fluid(500, 0.8442, 1.44, seed=15)
+    L = st.box[0]
+    out = oracle.run(st.pos, st.vel, st.image, L, 50, r_cut=2.5, r_skin=0.3, dt=0.005)
+    fb, _, _ = oracle.lj_forces(out["pos"], L, 2.5)
+    assert np.allclose(out["force"], fb, rtol=1e-12, atol=1e-11)
+
+
+def test_dpd_thermostat_temperature():
+    st = inputs.dpd_fluid(3000, 3.0, 1.0, seed=16)
+    L = st.box[0]
+    out = oracle.run(st.pos, st.vel, st.image, L, 600, r_cut=1.0, r_skin=0.3, dt=0.02,
+                     pair="dpd", coeff=[[25.0, 4.5]], kT=1.0, seed=5, thermo_period=10)
+    T = out["thermo"][20:, 4].mean()
+    assert T == pytest.approx(1.0, abs=0.05)
+    p = out["thermo"][:, 5:8]
+    assert np.abs(p).max() < 1e-9  # pairwise-symmetric noise conserves momentum
+
+
+# --------------------------------------------------------------------------
+# space-filling curve
+
+@pytest.mark.parametrize("bits", [1, 2, 3, 4])
+def test_hilbert_is_a_unit_step_bijection(bits):
+    m = 1 << bits
+    idx = {}
+    for x in range(m):
+        for y in range(m):
+            for z in range(m):
+                idx[oracle.hilbert3(x, y, z, bits)] = (x, y, z)
+    assert sorted(idx) == list(range(m ** 3))
+    for h in range(m ** 3 - 1):
+        a, b = np.array(idx[h]), np.array(idx[h + 1])
+        assert np.abs(a - b).sum() == 1
+    assert idx[0] == (0, 0, 0)
+
+
+def test_sfc_order_is_permutation_walking_adjacent_cells():
+    L = 12.0
+    nc = 4  # r_list 3.0 -> 4 cells of width 3
+    cells = np.array([(x, y, z) for x in range(nc) for y in range(nc) for z in range(nc)])
+    rng = np.random.default_rng(2)
+    perm = rng.permutation(len(cells))
+    pos = np.zeros((len(cells), 4))
+    pos[:, :3] = (cells[perm] + 0.5) * 3.0
+    order = oracle.sfc_order(pos, L, 3.0)
+    assert sorted(order.tolist()) == list(range(len(cells)))
+    walk = cells[perm][order]
+    assert np.all(np.abs(np.diff(walk, axis=0)).sum(1) == 1)
