@@ -1,0 +1,237 @@
+/*
+ * md.h -- C ABI of the GB300 short-range molecular-dynamics hot path.
+ *
+ * The library implements, on one GPU, the per-timestep path of the method of
+ * Glaser et al., "Strong scaling of general-purpose molecular dynamics
+ * simulations on GPUs" (HOOMD-blue 1.0): cell-list binning, a Verlet
+ * neighbour list with a buffer (skin) rebuilt when a particle moved more than
+ * half the buffer length, LJ and DPD pair forces, harmonic bonds and
+ * velocity-Verlet integration in a periodic box, for one system or for a
+ * batch of independent replicas in one launch per kernel.
+ *
+ * Conventions shared by every entry point
+ *   - Plain C: pointers, sizes and status codes; no C++ or framework types.
+ *   - "device" pointers are CUDA device memory owned by the caller; "host"
+ *     pointers are host memory read during the call only.
+ *   - Calls taking a stream only enqueue work on it and return without
+ *     synchronising, unless stated otherwise.  Argument errors are reported
+ *     immediately by the return code.  Errors found on the device (neighbour
+ *     row overflow, non-finite force) are recorded in a device error word
+ *     that md_poll_error() reads.
+ *   - The library never allocates device memory: the caller passes one
+ *     workspace buffer sized by md_workspace_size().  The system handle itself
+ *     lives in host memory owned by the library (md_destroy_system frees it).
+ *   - Indices are int32: at most 134,217,728 particles per system (neighbour
+ *     entries spend 5 of their 32 bits on the periodic image code).
+ *   - Units are LJ / DPD reduced units, k_B = 1.
+ */
+#ifndef MD_GB300_H
+#define MD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MD_ABI_VERSION 1
+
+typedef struct md_system md_system;
+typedef struct CUstream_st *md_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_INVALID_ARG = 1,          /* bad pointer, size or parameter */
+    MD_ERR_CUDA = 2,                 /* a CUDA runtime call failed */
+    MD_ERR_WORKSPACE_TOO_SMALL = 3,  /* ws_bytes < md_workspace_size() */
+    MD_ERR_NLIST_OVERFLOW = 4,       /* a neighbour row exceeded max_nb; detail = needed */
+    MD_ERR_CELL_GRID = 5,            /* fewer than 3 cells per box edge */
+    MD_ERR_NONFINITE = 6,            /* non-finite position after integration */
+    MD_ERR_CELL_OVERFLOW = 7,        /* a cell held more particles than can be ordered */
+    MD_ERR_STATE = 8                 /* call not valid in the current state */
+} md_status;
+
+typedef enum { MD_FP64 = 0, MD_MIXED = 1 } md_precision;
+typedef enum { MD_PAIR_LJ = 0, MD_PAIR_DPD = 1 } md_pair_kind;
+typedef enum { MD_KERNEL_NLIST = 0, MD_KERNEL_PAIR = 1 } md_kernel;
+
+/* Caller-owned particle state, all DEVICE arrays of N = n_total entries,
+ * concatenated over replicas (replica r owns [replica_offset[r],
+ * replica_offset[r+1])).  md_sort_particles permutes all five in place. */
+typedef struct {
+    double *pos;    /* [N][4] x, y, z in [0, L) of the particle's replica; w kept */
+    double *vel;    /* [N][4] vx, vy, vz; w kept */
+    int32_t *image; /* [N][4] periodic image counters; w kept */
+    int32_t *tag;   /* [N] global particle IDs: a permutation of 0..N-1 */
+    int32_t *type;  /* [N] particle type in [0, n_types) */
+} md_particles;
+
+/* Run parameters.  Paper references: list radius r_cut + r_buff and the
+ * half-buffer rebuild rule (Sec. 4.2); w threads per particle and the block
+ * size, set per kernel by md_autotune (Sec. 5.1-5.2). */
+typedef struct {
+    int64_t n_total;               /* N, summed over replicas */
+    int32_t n_replicas;            /* R >= 1 */
+    const int64_t *replica_offset; /* host [R+1], offset[0] = 0, offset[R] = N */
+    const double *box;             /* host [R][3] orthorhombic edge lengths */
+    double r_cut;                  /* pair cut-off */
+    double r_skin;                 /* buffer length r_buff (> 0) */
+    double dt;                     /* time step */
+    double mass;                   /* particle mass (all particles) */
+    double kT;                     /* DPD temperature */
+    uint64_t seed;                 /* DPD noise key */
+    int32_t pair;                  /* md_pair_kind */
+    int32_t n_types;               /* >= 1, <= 32 */
+    const double *pair_coeff;      /* host [n_types][n_types][2]:
+                                      LJ (epsilon, sigma); DPD (A, gamma) */
+    int32_t precision;             /* md_precision */
+    int32_t shift_energy;          /* LJ: report V(r) - V(r_cut) as energy */
+    int32_t max_nb;                /* neighbour row capacity (rounded up to 32) */
+    int32_t sort_period;           /* sort at the first rebuild >= this many
+                                      steps after the last sort; 0 = never */
+    int32_t thermo_period;         /* md_run: thermo row every this many steps;
+                                      0 = none */
+    int32_t graph_steps;           /* md_run: steps per captured CUDA graph
+                                      (multiple of thermo_period); 0 = eager */
+    int32_t max_bonds;             /* bonds per particle capacity; 0 = no bonds */
+} md_params;
+
+/* Thermodynamic row per replica, 8 doubles (Sec. 4.3.3 groups these global
+ * reductions into one synchronisation per step):
+ * {KE, PE, W, P, T, px, py, pz} = kinetic energy, potential energy, virial
+ * trace, pressure (2 KE + W) / (3 V), temperature 2 KE / (3 N - 3), momentum.
+ * PE and W are those of the last force evaluation made with want_virial = 1. */
+#define MD_THERMO_FIELDS 8
+
+int32_t md_abi_version(void);
+const char *md_status_string(md_status s);
+
+/* Bytes of device workspace a system with these parameters needs.
+ * Errors: MD_ERR_INVALID_ARG, MD_ERR_CELL_GRID. */
+md_status md_workspace_size(const md_params *p, size_t *bytes);
+
+/* Creates a system over caller-owned particle arrays and workspace (both must
+ * stay valid until md_destroy_system).  Builds the per-replica cell grids and
+ * space-filling-curve cell order on the host, uploads them, and binds `parts`.
+ * Enqueues initialisation on `stream`; does not build the neighbour list.
+ * Errors: MD_ERR_INVALID_ARG, MD_ERR_CELL_GRID, MD_ERR_WORKSPACE_TOO_SMALL,
+ * MD_ERR_CUDA. */
+md_status md_create_system(const md_params *p, const md_particles *parts,
+                           void *workspace, size_t ws_bytes, md_stream stream,
+                           md_system **out);
+
+/* Frees the host handle and any captured graph; the caller frees its memory. */
+md_status md_destroy_system(md_system *s);
+
+/* Harmonic bonds V = K/2 (r - r0)^2 between unordered pairs of particle IDs
+ * (tags) (Sec. 4.3.4: a bond is an unordered pair of particle IDs with a
+ * type).  bond_tags: HOST [n_bonds][2].  Stores, per particle ID, the IDs of
+ * its partners; fails with MD_ERR_INVALID_ARG if any particle has more than
+ * max_bonds partners.  Synchronises `stream`. */
+md_status md_set_bonds(md_system *s, const int32_t *bond_tags, int64_t n_bonds,
+                       double K, double r0, md_stream stream);
+
+/* Space-filling-curve sort: reorders every caller particle array so that
+ * particles follow the Hilbert order of their cells, ties by current index.
+ * force = 0: only replicas that rebuild now and whose last sort is
+ * >= sort_period steps old.  Requires md_build_cells to have binned the
+ * current positions (it sorts by that binning). */
+md_status md_sort_particles(md_system *s, int32_t force, md_stream stream);
+
+/* Cell-list binning (Sec. 4.3.3, Sec. 5.1): counts per cell, exclusive scan,
+ * scatter, then particles ordered by index inside each cell.  force = 0: only
+ * replicas whose rebuild flag was raised by md_integrate(half = 1). */
+md_status md_build_cells(md_system *s, int32_t force, md_stream stream);
+
+/* Neighbour list (Sec. 5.1, Fig. "nlist"): w threads per particle stride over
+ * the 27 cells around it and compact every j != i with
+ * |x_i - x_j|^2 < (r_cut + r_skin)^2 (minimum image, FP64 decision) into
+ * row i.  Records the build positions for the half-buffer test.
+ * force = 0: only replicas whose rebuild flag is raised.
+ * Row overflow: MD_ERR_NLIST_OVERFLOW in the device error word. */
+md_status md_build_nlist(md_system *s, int32_t force, md_stream stream);
+
+/* Pair forces from the neighbour list (Sec. 5.1: w threads per particle,
+ * intra-warp reduction).  LJ 12-6 or DPD (Groot-Warren, noise from
+ * Philox-4x32-10 keyed on (min tag, max tag, step, seed)), FP64 or mixed
+ * precision.  want_virial = 1 also writes per-particle energy and virial.
+ * Overwrites the force array. */
+md_status md_compute_pair(md_system *s, int32_t want_virial, md_stream stream);
+
+/* Adds harmonic-bond forces (md_set_bonds) to the force array. */
+md_status md_compute_bonds(md_system *s, int32_t want_virial, md_stream stream);
+
+/* Velocity Verlet (Sec. 3).  half = 1: v += dt/2 F/m, x += dt v, wrap into the
+ * box, advance the device step counter, and raise the replica's rebuild flag
+ * if a particle moved more than r_skin/2 since the last list build
+ * (Sec. 4.2).  half = 2: v += dt/2 F/m. */
+md_status md_integrate(md_system *s, int32_t half, md_stream stream);
+
+/* One full step: integrate(1), conditional sort / cells / nlist, pair, bonds,
+ * integrate(2). want_virial as in md_compute_pair. */
+md_status md_step(md_system *s, int32_t want_virial, md_stream stream);
+
+/* Thermo reduction (FP64, fixed summation tree: bitwise reproducible):
+ * writes R rows of MD_THERMO_FIELDS doubles to DEVICE memory dev_out. */
+md_status md_reduce_thermo(md_system *s, double *dev_out, md_stream stream);
+
+/* Runs n_steps full steps; segments of graph_steps steps replay one captured
+ * CUDA graph (captured on first use, re-captured after md_autotune or
+ * md_set_tuning).  If thermo_out (DEVICE, [n_steps / thermo_period][R][8]) is
+ * not NULL, a thermo row is written after every step t with
+ * t % thermo_period == 0, in order. */
+md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream stream);
+
+/* Autotuner (Sec. 5.2): for the pair and neighbour-list kernels, times every
+ * (block size b = 32 k <= 1024, threads per particle w = 2^m <= 32) pair,
+ * b >= w, with the median of n_samples launches (paper: 5), and keeps the
+ * fastest.  block_stride (>= 1) thins the block sizes to every block_stride-th
+ * multiple of 32.  Synchronises `stream`; rebuilds the neighbour list. */
+md_status md_autotune(md_system *s, int32_t n_samples, int32_t block_stride,
+                      md_stream stream);
+
+/* Sets / reads the launch parameters of one kernel (md_kernel).  Changing the
+ * pair kernel's w changes the list layout and forces a rebuild. */
+md_status md_set_tuning(md_system *s, int32_t kernel, int32_t block, int32_t w);
+md_status md_get_tuning(md_system *s, int32_t kernel, int32_t *block, int32_t *w);
+
+/* Device step counter (time step of the current positions). */
+md_status md_set_step(md_system *s, int64_t step, md_stream stream);
+md_status md_get_step(md_system *s, int64_t *step); /* synchronises */
+
+/* Synchronises the system's work and reads the device error word.  Returns
+ * MD_OK or the first recorded error; *detail gets the required max_nb for
+ * MD_ERR_NLIST_OVERFLOW, the particle index for MD_ERR_NONFINITE. */
+md_status md_poll_error(md_system *s, int64_t *detail);
+
+/* --- inspection (tests, diagnostics) ------------------------------------ */
+
+/* Forces as DEVICE double [N][4] (F, per-particle energy); virial (may be
+ * NULL) as DEVICE double [N][6] (xx, xy, xz, yy, yz, zz). */
+md_status md_get_forces(md_system *s, double *dev_force, double *dev_virial,
+                        md_stream stream);
+
+/* Neighbour rows as DEVICE int32 counts [N] and rows [N][max_nb] (plain
+ * particle indices; entries past counts[i] are -1). */
+md_status md_get_nlist(md_system *s, int32_t *dev_counts, int32_t *dev_rows,
+                       md_stream stream);
+
+/* Cell list as DEVICE arrays: cell_start / cell_count [total cells] (cells
+ * in Hilbert order per replica, replicas concatenated), cell_idx [N]. */
+md_status md_get_cells(md_system *s, int32_t *dev_start, int32_t *dev_count,
+                       int32_t *dev_idx, md_stream stream);
+
+/* Sizes: total cells, max_nb in use, number of list builds so far (syncs). */
+md_status md_get_info(md_system *s, int64_t *n_cells, int32_t *max_nb,
+                      int64_t *n_builds);
+
+/* The device Philox-4x32-10 used for the DPD noise, exposed for bitwise
+ * checks: in DEVICE [n][6] (ctr0..3, key0..1), out DEVICE [n][4]. */
+md_status md_philox4x32_10(const uint32_t *dev_in, uint32_t *dev_out, int64_t n,
+                           md_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MD_GB300_H */

@@ -1,0 +1,770 @@
+// C ABI of libmdgb (include/md.h): system set-up, workspace layout, the step
+// sequence, CUDA-graph capture of multi-step runs and the autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "md_internal.cuh"
+
+using namespace mdgb;
+
+namespace mdgb {
+cudaError_t launch_pair_span(const KArgs &a, Launch l, int want_virial, int span, cudaStream_t st);
+}
+
+struct md_system {
+  md_params p{};
+  std::vector<int64_t> off;
+  std::vector<double> box;
+  std::vector<double> coeff;
+  md_particles parts{};
+  KArgs a{};
+  std::vector<Rep> reps;
+  Launch tune[2]{{256, 8}, {256, 4}};  // nlist, pair
+  int span_pair = 1;
+  bool built = false;   // list built and forces computed (ready to step)
+  bool binned = false;  // cells binned at least once
+  bool listed = false;  // list built in the current layout
+  int64_t step = 0;
+  int64_t n_bonds = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool gvalid = false;
+};
+
+namespace {
+
+#define MD_CUDA(x)                                  \
+  do {                                              \
+    cudaError_t e_ = (x);                           \
+    if (e_ != cudaSuccess) return MD_ERR_CUDA;      \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int ilog2(int w) { int l = 0; while ((1 << l) < w) l++; return l; }
+
+// 3-D Hilbert index of cell (x, y, z) on a 2^bits grid (Skilling, AIP Conf.
+// Proc. 707, 2004).  The coordinates are turned into the curve's "transposed"
+// index by walking the bit levels from the top, reflecting or exchanging the
+// lower bits at each level; a Gray decode across the axes and the bit
+// interleave then give the index.  Written independently of the oracle's copy.
+uint64_t hilbert_key(uint32_t x, uint32_t y, uint32_t z, int bits) {
+  uint32_t c[3] = {x, y, z};
+  for (int lvl = bits - 1; lvl >= 1; --lvl) {
+    const uint32_t bit = 1u << lvl, below = bit - 1u;
+    for (int ax = 0; ax < 3; ++ax) {
+      if (c[ax] & bit) {
+        c[0] ^= below;  // reflect axis 0's lower bits
+      } else {
+        const uint32_t swap = (c[0] ^ c[ax]) & below;  // exchange lower bits
+        c[0] ^= swap;
+        c[ax] ^= swap;
+      }
+    }
+  }
+  for (int ax = 1; ax < 3; ++ax) c[ax] ^= c[ax - 1];
+  uint32_t mask = 0;
+  for (int lvl = bits - 1; lvl >= 1; --lvl)
+    if (c[2] & (1u << lvl)) mask ^= (1u << lvl) - 1u;
+  for (int ax = 0; ax < 3; ++ax) c[ax] ^= mask;
+  uint64_t key = 0;
+  for (int lvl = bits - 1; lvl >= 0; --lvl)
+    for (int ax = 0; ax < 3; ++ax) key = (key << 1) | ((c[ax] >> lvl) & 1u);
+  return key;
+}
+
+struct Plan {
+  std::vector<Rep> reps;
+  int64_t n = 0, n_pad = 0, n_cells = 0, n_chunks = 0, n_tchunks = 0;
+  int32_t max_nb = 0;
+  // byte offsets into the workspace
+  size_t o_rep, o_off, o_chunk_rep, o_tchunk_rep, o_cell_rank, o_cell_count, o_cell_start,
+      o_chunk_sum, o_cell_idx, o_pcell, o_pslot, o_n_nb, o_rtag, o_pos4f, o_oref, o_vel4f, o_nl,
+      o_force, o_virial, o_tpart, o_ds, o_rebuild, o_sort_now, o_last_sort, o_coeff, o_btab,
+      o_s_pos, o_s_vel, o_s_img, o_s_tag, o_s_type, o_s_pos4f, o_s_oref, o_s_vel4f;
+  size_t total = 0;
+};
+
+md_status validate(const md_params *p) {
+  if (!p) return MD_ERR_INVALID_ARG;
+  if (p->n_total < 0 || p->n_total > kMaxParticles) return MD_ERR_INVALID_ARG;
+  if (p->n_replicas < 1 || !p->replica_offset || !p->box) return MD_ERR_INVALID_ARG;
+  if (p->replica_offset[0] != 0 || p->replica_offset[p->n_replicas] != p->n_total)
+    return MD_ERR_INVALID_ARG;
+  for (int r = 0; r < p->n_replicas; r++)
+    if (p->replica_offset[r + 1] < p->replica_offset[r]) return MD_ERR_INVALID_ARG;
+  if (!(p->r_cut > 0) || !(p->r_skin > 0) || !(p->dt > 0) || !(p->mass > 0))
+    return MD_ERR_INVALID_ARG;
+  if (!std::isfinite(p->r_cut) || !std::isfinite(p->r_skin) || !std::isfinite(p->dt))
+    return MD_ERR_INVALID_ARG;
+  if (p->pair != MD_PAIR_LJ && p->pair != MD_PAIR_DPD) return MD_ERR_INVALID_ARG;
+  if (p->precision != MD_FP64 && p->precision != MD_MIXED) return MD_ERR_INVALID_ARG;
+  if (p->n_types < 1 || p->n_types > kMaxTypes || !p->pair_coeff) return MD_ERR_INVALID_ARG;
+  if (p->pair == MD_PAIR_DPD && !(p->kT >= 0)) return MD_ERR_INVALID_ARG;
+  if (p->max_nb < 1 || p->max_nb > (1 << 20)) return MD_ERR_INVALID_ARG;
+  if (p->sort_period < 0 || p->thermo_period < 0 || p->graph_steps < 0 || p->max_bonds < 0)
+    return MD_ERR_INVALID_ARG;
+  if (p->graph_steps > 0 && p->thermo_period > 0 && p->graph_steps % p->thermo_period != 0)
+    return MD_ERR_INVALID_ARG;
+  for (int k = 0; k < 3 * p->n_replicas; k++)
+    if (!(p->box[k] > 0) || !std::isfinite(p->box[k])) return MD_ERR_INVALID_ARG;
+  return MD_OK;
+}
+
+md_status make_plan(const md_params *p, Plan &pl) {
+  md_status st = validate(p);
+  if (st != MD_OK) return st;
+  const int R = p->n_replicas;
+  const double rl = p->r_cut + p->r_skin;
+  pl.n = p->n_total;
+  pl.n_pad = std::max<int64_t>(128, (p->n_total + 127) / 128 * 128);
+  pl.max_nb = (p->max_nb + 31) / 32 * 32;
+  pl.reps.resize(R);
+  int64_t cell0 = 0, chunk0 = 0, tchunk0 = 0;
+  for (int r = 0; r < R; r++) {
+    Rep &rp = pl.reps[r];
+    std::memset(&rp, 0, sizeof(rp));
+    rp.p0 = p->replica_offset[r];
+    rp.p1 = p->replica_offset[r + 1];
+    double hmax = 0;
+    for (int d = 0; d < 3; d++) {
+      const double L = p->box[3 * r + d];
+      double m = std::floor(L / rl);
+      if (m > 512.0) m = 512.0;
+      if (m < 3.0) return MD_ERR_CELL_GRID;
+      rp.nc[d] = (int32_t)m;
+      rp.L[d] = L;
+      rp.inv_L[d] = 1.0 / L;
+      rp.h[d] = L / (double)rp.nc[d];
+      rp.inv_h[d] = (double)rp.nc[d] / L;
+      rp.hf[d] = (float)rp.h[d];
+      hmax = std::max(hmax, rp.h[d]);
+    }
+    // FP32 r^2 error bound: |o| <= (h + skin) / 2 per coordinate; each
+    // separation component carries at most ~7 roundings of 2^-24 (h + skin),
+    // so |dr^2| < 28 * 2^-24 (h + skin)^2; the band doubles that.
+    rp.band = (float)(64.0 * std::ldexp(1.0, -24) * (hmax + p->r_skin) * (hmax + p->r_skin));
+    rp.volume = rp.L[0] * rp.L[1] * rp.L[2];
+    rp.ncell = rp.nc[0] * rp.nc[1] * rp.nc[2];
+    rp.nchunk = (rp.ncell + kChunkCells - 1) / kChunkCells;
+    const int64_t np = rp.p1 - rp.p0;
+    rp.ntchunk = (int32_t)((np + kThermoChunk - 1) / kThermoChunk);
+    rp.cell0 = cell0;
+    rp.chunk0 = chunk0;
+    rp.tchunk0 = tchunk0;
+    cell0 += (int64_t)rp.nchunk * kChunkCells;
+    chunk0 += rp.nchunk;
+    tchunk0 += rp.ntchunk;
+  }
+  pl.n_cells = cell0;
+  pl.n_chunks = chunk0;
+  pl.n_tchunks = tchunk0;
+  const bool mixed = p->precision == MD_MIXED;
+  const bool dpd = p->pair == MD_PAIR_DPD;
+  const int64_t N = pl.n, NP = pl.n_pad;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align256(o + std::max<size_t>(bytes, 1)); return at; };
+  pl.o_rep = take(sizeof(Rep) * R);
+  pl.o_off = take(sizeof(int64_t) * (R + 1));
+  pl.o_chunk_rep = take(sizeof(int32_t) * pl.n_chunks);
+  pl.o_tchunk_rep = take(sizeof(int32_t) * pl.n_tchunks);
+  pl.o_cell_rank = take(sizeof(int32_t) * pl.n_cells);
+  pl.o_cell_count = take(sizeof(int32_t) * pl.n_cells);
+  pl.o_cell_start = take(sizeof(int32_t) * pl.n_cells);
+  pl.o_chunk_sum = take(sizeof(int32_t) * pl.n_chunks);
+  pl.o_cell_idx = take(sizeof(int32_t) * N);
+  pl.o_pcell = take(sizeof(int32_t) * N);
+  pl.o_pslot = take(sizeof(int32_t) * N);
+  pl.o_n_nb = take(sizeof(int32_t) * NP);
+  pl.o_rtag = take(sizeof(int32_t) * N);
+  pl.o_pos4f = take(sizeof(float4) * NP);
+  pl.o_oref = take(sizeof(float4) * NP);
+  pl.o_vel4f = dpd ? take(sizeof(float4) * NP) : 0;
+  pl.o_nl = take(sizeof(uint32_t) * (size_t)pl.max_nb * NP);
+  pl.o_force = take((mixed ? sizeof(float4) : sizeof(double4)) * NP);
+  pl.o_virial = take((mixed ? sizeof(float) : sizeof(double)) * 6 * NP);
+  pl.o_tpart = take(sizeof(double) * 8 * pl.n_tchunks);
+  pl.o_ds = take(sizeof(DevState));
+  pl.o_rebuild = take(sizeof(int32_t) * 2 * R);
+  pl.o_sort_now = take(sizeof(int32_t) * R);
+  pl.o_last_sort = take(sizeof(int64_t) * R);
+  pl.o_coeff = take(64 * (size_t)p->n_types * p->n_types);
+  pl.o_btab = take(sizeof(int32_t) * (size_t)std::max(p->max_bonds, 0) * N);
+  pl.o_s_pos = take(sizeof(double4) * N);
+  pl.o_s_vel = take(sizeof(double4) * N);
+  pl.o_s_img = take(sizeof(int4) * N);
+  pl.o_s_tag = take(sizeof(int32_t) * N);
+  pl.o_s_type = take(sizeof(int32_t) * N);
+  pl.o_s_pos4f = take(sizeof(float4) * N);
+  pl.o_s_oref = take(sizeof(float4) * N);
+  pl.o_s_vel4f = dpd ? take(sizeof(float4) * N) : 0;
+  pl.total = o;
+  return MD_OK;
+}
+
+template <class T>
+T *at(void *base, size_t off) { return reinterpret_cast<T *>(static_cast<char *>(base) + off); }
+
+md_status enqueue_step(md_system *s, int want_virial, cudaStream_t st) {
+  const KArgs &a = s->a;
+  MD_CUDA(launch_integrate1(a, st));
+  MD_CUDA(launch_bin(a, 0, st));
+  if (s->p.sort_period > 0) MD_CUDA(launch_sort(a, 0, st));
+  MD_CUDA(launch_nlist(a, s->tune[MD_KERNEL_NLIST], 0, st));
+  MD_CUDA(launch_pair_span(a, s->tune[MD_KERNEL_PAIR], want_virial, s->span_pair, st));
+  if (s->n_bonds > 0) MD_CUDA(launch_bonds(a, want_virial, st));
+  MD_CUDA(launch_integrate2(a, st));
+  return MD_OK;
+}
+
+md_status prepare(md_system *s, cudaStream_t st) {
+  if (s->built) return MD_OK;
+  MD_CUDA(launch_bin(s->a, 1, st));
+  s->binned = true;
+  MD_CUDA(launch_nlist(s->a, s->tune[MD_KERNEL_NLIST], 1, st));
+  s->listed = true;
+  MD_CUDA(launch_pair_span(s->a, s->tune[MD_KERNEL_PAIR], 0, s->span_pair, st));
+  if (s->n_bonds > 0) MD_CUDA(launch_bonds(s->a, 0, st));
+  s->built = true;
+  return MD_OK;
+}
+
+void set_pair_w(md_system *s, Launch l) {
+  s->tune[MD_KERNEL_PAIR] = l;
+  s->a.w_store_log2 = ilog2(l.w);
+  s->span_pair = pair_span(s->off.data(), s->p.n_replicas, s->a.n, l.block / l.w);
+  s->gvalid = false;
+}
+
+bool valid_launch(int block, int w) {
+  return block >= 32 && block <= 1024 && block % 32 == 0 &&
+         (w == 1 || w == 2 || w == 4 || w == 8 || w == 16 || w == 32);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t md_abi_version(void) { return MD_ABI_VERSION; }
+
+const char *md_status_string(md_status s) {
+  switch (s) {
+    case MD_OK: return "ok";
+    case MD_ERR_INVALID_ARG: return "invalid argument";
+    case MD_ERR_CUDA: return "CUDA runtime error";
+    case MD_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case MD_ERR_NLIST_OVERFLOW: return "neighbour row overflow (raise max_nb)";
+    case MD_ERR_CELL_GRID: return "box smaller than 3 cells of r_cut + r_skin per edge";
+    case MD_ERR_NONFINITE: return "non-finite particle position";
+    case MD_ERR_CELL_OVERFLOW: return "cell occupancy above the in-cell sort limit";
+    case MD_ERR_STATE: return "call not valid in the current state";
+  }
+  return "unknown status";
+}
+
+md_status md_workspace_size(const md_params *p, size_t *bytes) {
+  if (!bytes) return MD_ERR_INVALID_ARG;
+  Plan pl;
+  md_status st = make_plan(p, pl);
+  if (st != MD_OK) return st;
+  *bytes = pl.total;
+  return MD_OK;
+}
+
+md_status md_create_system(const md_params *p, const md_particles *parts, void *workspace,
+                           size_t ws_bytes, md_stream stream_, md_system **out) {
+  if (!out || !parts) return MD_ERR_INVALID_ARG;
+  *out = nullptr;
+  Plan pl;
+  md_status st = make_plan(p, pl);
+  if (st != MD_OK) return st;
+  if (!workspace || ws_bytes < pl.total) return MD_ERR_WORKSPACE_TOO_SMALL;
+  if (((uintptr_t)workspace & 255) != 0) return MD_ERR_INVALID_ARG;
+  if (p->n_total > 0 && (!parts->pos || !parts->vel || !parts->image || !parts->tag || !parts->type))
+    return MD_ERR_INVALID_ARG;
+  if (((uintptr_t)parts->pos & 15) || ((uintptr_t)parts->vel & 15) || ((uintptr_t)parts->image & 15))
+    return MD_ERR_INVALID_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+
+  md_system *s = new (std::nothrow) md_system();
+  if (!s) return MD_ERR_INVALID_ARG;
+  s->p = *p;
+  const int R = p->n_replicas;
+  s->off.assign(p->replica_offset, p->replica_offset + R + 1);
+  s->box.assign(p->box, p->box + 3 * R);
+  s->coeff.assign(p->pair_coeff, p->pair_coeff + 2 * p->n_types * p->n_types);
+  s->p.replica_offset = s->off.data();
+  s->p.box = s->box.data();
+  s->p.pair_coeff = s->coeff.data();
+  s->p.max_nb = pl.max_nb;
+  s->parts = *parts;
+  s->reps = pl.reps;
+
+  KArgs &a = s->a;
+  std::memset(&a, 0, sizeof(a));
+  void *ws = workspace;
+  const bool mixed = p->precision == MD_MIXED, dpd = p->pair == MD_PAIR_DPD;
+  a.n = pl.n;
+  a.n_pad = pl.n_pad;
+  a.R = R;
+  a.ntypes = p->n_types;
+  a.rep_off = at<int64_t>(ws, pl.o_off);
+  a.rep = at<Rep>(ws, pl.o_rep);
+  a.chunk_rep = at<int32_t>(ws, pl.o_chunk_rep);
+  a.tchunk_rep = at<int32_t>(ws, pl.o_tchunk_rep);
+  a.pos = reinterpret_cast<double4 *>(parts->pos);
+  a.vel = reinterpret_cast<double4 *>(parts->vel);
+  a.image = reinterpret_cast<int4 *>(parts->image);
+  a.tag = parts->tag;
+  a.type = parts->type;
+  a.pos4f = at<float4>(ws, pl.o_pos4f);
+  a.oref = at<float4>(ws, pl.o_oref);
+  a.vel4f = dpd ? at<float4>(ws, pl.o_vel4f) : nullptr;
+  a.cell_rank = at<int32_t>(ws, pl.o_cell_rank);
+  a.cell_count = at<int32_t>(ws, pl.o_cell_count);
+  a.cell_start = at<int32_t>(ws, pl.o_cell_start);
+  a.chunk_sum = at<int32_t>(ws, pl.o_chunk_sum);
+  a.cell_idx = at<int32_t>(ws, pl.o_cell_idx);
+  a.pcell = at<int32_t>(ws, pl.o_pcell);
+  a.pslot = at<int32_t>(ws, pl.o_pslot);
+  a.nl = at<uint32_t>(ws, pl.o_nl);
+  a.n_nb = at<int32_t>(ws, pl.o_n_nb);
+  a.force = at<void>(ws, pl.o_force);
+  a.virial = at<void>(ws, pl.o_virial);
+  a.tpart = at<double>(ws, pl.o_tpart);
+  a.ds = at<DevState>(ws, pl.o_ds);
+  a.rebuild = at<int32_t>(ws, pl.o_rebuild);
+  a.sort_now = at<int32_t>(ws, pl.o_sort_now);
+  a.last_sort = at<int64_t>(ws, pl.o_last_sort);
+  a.rtag = at<int32_t>(ws, pl.o_rtag);
+  a.btab = p->max_bonds > 0 ? at<int32_t>(ws, pl.o_btab) : nullptr;
+  a.s_pos = at<double4>(ws, pl.o_s_pos);
+  a.s_vel = at<double4>(ws, pl.o_s_vel);
+  a.s_img = at<int4>(ws, pl.o_s_img);
+  a.s_tag = at<int32_t>(ws, pl.o_s_tag);
+  a.s_type = at<int32_t>(ws, pl.o_s_type);
+  a.s_pos4f = at<float4>(ws, pl.o_s_pos4f);
+  a.s_oref = at<float4>(ws, pl.o_s_oref);
+  a.s_vel4f = dpd ? at<float4>(ws, pl.o_s_vel4f) : nullptr;
+  a.coeff = at<void>(ws, pl.o_coeff);
+  a.max_nb = pl.max_nb;
+  a.sort_period = p->sort_period;
+  a.max_bonds = p->max_bonds;
+  a.mixed = mixed;
+  a.pair = p->pair;
+  const double rl = p->r_cut + p->r_skin;
+  a.r_cut = p->r_cut;
+  a.rc2 = p->r_cut * p->r_cut;
+  a.rl2 = rl * rl;
+  a.rc2f = (float)a.rc2;
+  a.rl2f = (float)a.rl2;
+  a.dt = p->dt;
+  a.mass = p->mass;
+  a.kT = p->kT;
+  a.seed = p->seed;
+  a.disp2_f = (float)(0.25 * p->r_skin * p->r_skin * (1.0 - 1e-4));
+  a.n_chunks = pl.n_chunks;
+  a.n_tchunks = pl.n_tchunks;
+  a.n_cells = pl.n_cells;
+
+  // host tables
+  std::vector<int32_t> chunk_rep(pl.n_chunks), tchunk_rep(pl.n_tchunks);
+  std::vector<int32_t> rank(pl.n_cells, 0);
+  for (int r = 0; r < R; r++) {
+    const Rep &rp = pl.reps[r];
+    for (int c = 0; c < rp.nchunk; c++) chunk_rep[rp.chunk0 + c] = r;
+    for (int c = 0; c < rp.ntchunk; c++) tchunk_rep[rp.tchunk0 + c] = r;
+    const int nmax = std::max(rp.nc[0], std::max(rp.nc[1], rp.nc[2]));
+    int bits = 1;
+    while ((1 << bits) < nmax) bits++;
+    std::vector<std::pair<uint64_t, int32_t>> keys(rp.ncell);
+    for (int z = 0; z < rp.nc[2]; z++)
+      for (int y = 0; y < rp.nc[1]; y++)
+        for (int x = 0; x < rp.nc[0]; x++) {
+          const int32_t lin = x + rp.nc[0] * (y + rp.nc[1] * z);
+          keys[lin] = {hilbert_key(x, y, z, bits), lin};
+        }
+    std::sort(keys.begin(), keys.end());
+    for (int32_t k = 0; k < rp.ncell; k++) rank[rp.cell0 + keys[k].second] = k;
+  }
+  std::vector<unsigned char> coeff(64 * (size_t)p->n_types * p->n_types, 0);
+  for (int ti = 0; ti < p->n_types; ti++)
+    for (int tj = 0; tj < p->n_types; tj++) {
+      const int c = ti * p->n_types + tj;
+      const double c0 = p->pair_coeff[2 * c], c1 = p->pair_coeff[2 * c + 1];
+      if (p->pair == MD_PAIR_LJ) {
+        const double eps = c0, sig = c1;
+        const double s6 = std::pow(sig, 6), s12 = s6 * s6;
+        const double sr6 = s6 / std::pow(p->r_cut, 6);
+        const double vc = p->shift_energy ? 4.0 * eps * (sr6 * sr6 - sr6) : 0.0;
+        if (mixed) {
+          LJCoeffF f{(float)(48 * eps * s12), (float)(24 * eps * s6), (float)(4 * eps * s12),
+                     (float)(4 * eps * s6), (float)vc, 0, 0, 0};
+          std::memcpy(coeff.data() + sizeof(LJCoeffF) * c, &f, sizeof(f));
+        } else {
+          LJCoeffD d{48 * eps * s12, 24 * eps * s6, 4 * eps * s12, 4 * eps * s6, vc, 0, 0, 0};
+          std::memcpy(coeff.data() + sizeof(LJCoeffD) * c, &d, sizeof(d));
+        }
+      } else {
+        const double A = c0, gamma = c1;
+        const double srdt = std::sqrt(2.0 * gamma * p->kT) / std::sqrt(p->dt);
+        if (mixed) {
+          DPDCoeffF f{(float)A, (float)gamma, (float)srdt, 0};
+          std::memcpy(coeff.data() + sizeof(DPDCoeffF) * c, &f, sizeof(f));
+        } else {
+          DPDCoeffD d{A, gamma, srdt, 0};
+          std::memcpy(coeff.data() + sizeof(DPDCoeffD) * c, &d, sizeof(d));
+        }
+      }
+    }
+
+  auto fail = [&](md_status e) { delete s; return e; };
+  if (cudaMemcpyAsync(at<void>(ws, pl.o_rep), pl.reps.data(), sizeof(Rep) * R, cudaMemcpyHostToDevice, stream) ||
+      cudaMemcpyAsync(at<void>(ws, pl.o_off), s->off.data(), sizeof(int64_t) * (R + 1), cudaMemcpyHostToDevice, stream) ||
+      cudaMemcpyAsync(at<void>(ws, pl.o_chunk_rep), chunk_rep.data(), sizeof(int32_t) * pl.n_chunks, cudaMemcpyHostToDevice, stream) ||
+      cudaMemcpyAsync(at<void>(ws, pl.o_tchunk_rep), tchunk_rep.data(), sizeof(int32_t) * pl.n_tchunks, cudaMemcpyHostToDevice, stream) ||
+      cudaMemcpyAsync(at<void>(ws, pl.o_cell_rank), rank.data(), sizeof(int32_t) * pl.n_cells, cudaMemcpyHostToDevice, stream) ||
+      cudaMemcpyAsync(at<void>(ws, pl.o_coeff), coeff.data(), coeff.size(), cudaMemcpyHostToDevice, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_cell_count), 0, sizeof(int32_t) * pl.n_cells, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_cell_start), 0, sizeof(int32_t) * pl.n_cells, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_n_nb), 0, sizeof(int32_t) * pl.n_pad, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_nl), 0, sizeof(uint32_t) * (size_t)pl.max_nb * pl.n_pad, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_rtag), 0, sizeof(int32_t) * pl.n, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_pcell), 0, sizeof(int32_t) * pl.n, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_pslot), 0, sizeof(int32_t) * pl.n, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_force), 0, (mixed ? 16 : 32) * pl.n_pad, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_virial), 0, (mixed ? 4 : 8) * 6 * pl.n_pad, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_ds), 0, sizeof(DevState), stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_rebuild), 0, sizeof(int32_t) * 2 * R, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_sort_now), 0, sizeof(int32_t) * R, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_last_sort), 0, sizeof(int64_t) * R, stream))
+    return fail(MD_ERR_CUDA);
+  if (p->max_bonds > 0 &&
+      cudaMemsetAsync(at<void>(ws, pl.o_btab), 0xff, sizeof(int32_t) * (size_t)p->max_bonds * pl.n, stream))
+    return fail(MD_ERR_CUDA);
+  if (launch_init_frames(a, stream) != cudaSuccess) return fail(MD_ERR_CUDA);
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return fail(MD_ERR_CUDA);
+  uint32_t err = 0;
+  if (cudaMemcpy(&err, &a.ds->error, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(MD_ERR_CUDA);
+  if (err & kErrBadInput) return fail(MD_ERR_INVALID_ARG);
+  if (cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(MD_ERR_CUDA);
+  set_pair_w(s, s->tune[MD_KERNEL_PAIR]);
+  *out = s;
+  return MD_OK;
+}
+
+md_status md_destroy_system(md_system *s) {
+  if (!s) return MD_ERR_INVALID_ARG;
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->cap) cudaStreamDestroy(s->cap);
+  delete s;
+  return MD_OK;
+}
+
+md_status md_set_bonds(md_system *s, const int32_t *bond_tags, int64_t n_bonds, double K,
+                       double r0, md_stream stream_) {
+  if (!s || n_bonds < 0 || (n_bonds > 0 && !bond_tags)) return MD_ERR_INVALID_ARG;
+  if (n_bonds > 0 && s->p.max_bonds == 0) return MD_ERR_INVALID_ARG;
+  if (!(K >= 0) || !(r0 >= 0)) return MD_ERR_INVALID_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  const int64_t N = s->a.n;
+  const int mb = s->p.max_bonds;
+  if (mb > 0) {
+    std::vector<int32_t> tab((size_t)N * mb, -1);
+    std::vector<int32_t> cnt(N, 0);
+    for (int64_t b = 0; b < n_bonds; b++) {
+      const int32_t x = bond_tags[2 * b], y = bond_tags[2 * b + 1];
+      if (x < 0 || y < 0 || x >= N || y >= N || x == y) return MD_ERR_INVALID_ARG;
+      if (cnt[x] >= mb || cnt[y] >= mb) return MD_ERR_INVALID_ARG;
+      tab[(size_t)x * mb + cnt[x]++] = y;
+      tab[(size_t)y * mb + cnt[y]++] = x;
+    }
+    MD_CUDA(cudaMemcpyAsync(s->a.btab, tab.data(), sizeof(int32_t) * tab.size(),
+                            cudaMemcpyHostToDevice, stream));
+    MD_CUDA(cudaStreamSynchronize(stream));
+  }
+  s->n_bonds = n_bonds;
+  s->a.bond_K = K;
+  s->a.bond_r0 = r0;
+  s->gvalid = false;
+  s->built = false;  // forces must include the bonds before the next step
+  return MD_OK;
+}
+
+md_status md_sort_particles(md_system *s, int32_t force, md_stream stream) {
+  if (!s) return MD_ERR_INVALID_ARG;
+  if (!s->binned) return MD_ERR_STATE;
+  MD_CUDA(launch_sort(s->a, force ? 1 : 0, reinterpret_cast<cudaStream_t>(stream)));
+  return MD_OK;
+}
+
+md_status md_build_cells(md_system *s, int32_t force, md_stream stream) {
+  if (!s) return MD_ERR_INVALID_ARG;
+  MD_CUDA(launch_bin(s->a, force ? 1 : 0, reinterpret_cast<cudaStream_t>(stream)));
+  if (force) s->binned = true;
+  return MD_OK;
+}
+
+md_status md_build_nlist(md_system *s, int32_t force, md_stream stream) {
+  if (!s) return MD_ERR_INVALID_ARG;
+  if (!s->binned) return MD_ERR_STATE;
+  MD_CUDA(launch_nlist(s->a, s->tune[MD_KERNEL_NLIST], force ? 1 : 0,
+                       reinterpret_cast<cudaStream_t>(stream)));
+  if (force) s->listed = true;
+  return MD_OK;
+}
+
+md_status md_compute_pair(md_system *s, int32_t want_virial, md_stream stream) {
+  if (!s) return MD_ERR_INVALID_ARG;
+  if (!s->listed) return MD_ERR_STATE;  // no list in the current layout yet
+  MD_CUDA(launch_pair_span(s->a, s->tune[MD_KERNEL_PAIR], want_virial ? 1 : 0, s->span_pair,
+                           reinterpret_cast<cudaStream_t>(stream)));
+  return MD_OK;
+}
+
+md_status md_compute_bonds(md_system *s, int32_t want_virial, md_stream stream) {
+  if (!s) return MD_ERR_INVALID_ARG;
+  if (s->n_bonds == 0) return MD_OK;
+  MD_CUDA(launch_bonds(s->a, want_virial ? 1 : 0, reinterpret_cast<cudaStream_t>(stream)));
+  return MD_OK;
+}
+
+md_status md_integrate(md_system *s, int32_t half, md_stream stream) {
+  if (!s || (half != 1 && half != 2)) return MD_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (half == 1) {
+    MD_CUDA(launch_integrate1(s->a, st));
+    s->step++;
+  } else {
+    MD_CUDA(launch_integrate2(s->a, st));
+  }
+  return MD_OK;
+}
+
+md_status md_step(md_system *s, int32_t want_virial, md_stream stream) {
+  if (!s) return MD_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  md_status e = prepare(s, st);
+  if (e != MD_OK) return e;
+  e = enqueue_step(s, want_virial ? 1 : 0, st);
+  if (e == MD_OK) s->step++;
+  return e;
+}
+
+md_status md_reduce_thermo(md_system *s, double *dev_out, md_stream stream) {
+  if (!s || !dev_out) return MD_ERR_INVALID_ARG;
+  MD_CUDA(launch_thermo(s->a, dev_out, 0, reinterpret_cast<cudaStream_t>(stream)));
+  return MD_OK;
+}
+
+md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream stream) {
+  if (!s || n_steps < 0) return MD_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  md_status e = prepare(s, st);
+  if (e != MD_OK) return e;
+  const int64_t period = s->p.thermo_period;
+  const int gsteps = s->p.graph_steps;
+  const int64_t rows = period > 0 ? (s->step + n_steps) / period - s->step / period : 0;
+  MD_CUDA(launch_run_begin(s->a, thermo_out, period, rows, st));
+  int64_t left = n_steps;
+  while (left > 0) {
+    if (gsteps > 0 && left >= gsteps && (period == 0 || s->step % period == 0)) {
+      if (!s->gvalid) {
+        if (s->gexec) { cudaGraphExecDestroy(s->gexec); s->gexec = nullptr; }
+        cudaGraph_t g = nullptr;
+        MD_CUDA(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+        md_status ce = MD_OK;
+        for (int l = 0; l < gsteps && ce == MD_OK; l++) {
+          const int th = period > 0 && (l + 1) % period == 0;
+          ce = enqueue_step(s, th, s->cap);
+          if (ce == MD_OK && th && launch_thermo(s->a, nullptr, 1, s->cap) != cudaSuccess) ce = MD_ERR_CUDA;
+        }
+        cudaError_t ee = cudaStreamEndCapture(s->cap, &g);
+        if (ce != MD_OK) { if (g) cudaGraphDestroy(g); return ce; }
+        if (ee != cudaSuccess) return MD_ERR_CUDA;
+        cudaError_t ie = cudaGraphInstantiate(&s->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) { s->gexec = nullptr; return MD_ERR_CUDA; }
+        s->gvalid = true;
+      }
+      MD_CUDA(cudaGraphLaunch(s->gexec, st));
+      s->step += gsteps;
+      left -= gsteps;
+    } else {
+      const int th = period > 0 && (s->step + 1) % period == 0;
+      e = enqueue_step(s, th, st);
+      if (e != MD_OK) return e;
+      if (th) MD_CUDA(launch_thermo(s->a, nullptr, 1, st));
+      s->step++;
+      left--;
+    }
+  }
+  return MD_OK;
+}
+
+md_status md_set_tuning(md_system *s, int32_t kernel, int32_t block, int32_t w) {
+  if (!s || (kernel != MD_KERNEL_NLIST && kernel != MD_KERNEL_PAIR) || !valid_launch(block, w))
+    return MD_ERR_INVALID_ARG;
+  const int mb = kernel == MD_KERNEL_NLIST
+                     ? max_block_nlist(w)
+                     : std::min(max_block_pair(s->a, w, 0), max_block_pair(s->a, w, 1));
+  if (block > mb) return MD_ERR_INVALID_ARG;
+  if (kernel == MD_KERNEL_NLIST) {
+    s->tune[MD_KERNEL_NLIST] = Launch{block, w};
+    s->gvalid = false;
+  } else {
+    const bool relayout = w != s->tune[MD_KERNEL_PAIR].w;
+    set_pair_w(s, Launch{block, w});
+    if (relayout) s->built = s->listed = false;  // rows must be rewritten in the new layout
+  }
+  return MD_OK;
+}
+
+md_status md_get_tuning(md_system *s, int32_t kernel, int32_t *block, int32_t *w) {
+  if (!s || !block || !w || (kernel != MD_KERNEL_NLIST && kernel != MD_KERNEL_PAIR))
+    return MD_ERR_INVALID_ARG;
+  *block = s->tune[kernel].block;
+  *w = s->tune[kernel].w;
+  return MD_OK;
+}
+
+md_status md_autotune(md_system *s, int32_t n_samples, int32_t block_stride, md_stream stream) {
+  if (!s || n_samples < 1 || block_stride < 1) return MD_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  md_status e = prepare(s, st);
+  if (e != MD_OK) return e;
+  cudaEvent_t e0, e1;
+  MD_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MD_ERR_CUDA; }
+  auto median_time = [&](auto &&launch) -> float {
+    std::vector<float> t;
+    for (int k = 0; k < n_samples; k++) {
+      cudaEventRecord(e0, st);
+      if (launch() != cudaSuccess) return -1.f;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    return t[t.size() / 2];
+  };
+  static const int ws[6] = {1, 2, 4, 8, 16, 32};
+  md_status result = MD_OK;
+  // pair kernel: (block, w); each w needs its own list layout
+  Launch best_pair = s->tune[MD_KERNEL_PAIR];
+  float best_t = 1e30f;
+  for (int w : ws) {
+    set_pair_w(s, Launch{std::max(32, w), w});
+    if (launch_nlist(s->a, s->tune[MD_KERNEL_NLIST], 1, st) != cudaSuccess) { result = MD_ERR_CUDA; break; }
+    const int mb = std::min(max_block_pair(s->a, w, 0), max_block_pair(s->a, w, 1));
+    for (int b = 32 * block_stride; b <= std::min(1024, mb); b += 32 * block_stride) {
+      if (b < w) continue;
+      set_pair_w(s, Launch{b, w});
+      const float t = median_time([&] { return launch_pair_span(s->a, Launch{b, w}, 0, s->span_pair, st); });
+      if (t < 0) { cudaGetLastError(); continue; }
+      if (t < best_t) { best_t = t; best_pair = Launch{b, w}; }
+    }
+  }
+  set_pair_w(s, best_pair);
+  // neighbour-list kernel: (block, w) over the chosen layout
+  Launch best_nl = s->tune[MD_KERNEL_NLIST];
+  best_t = 1e30f;
+  for (int w : ws) {
+    if (result != MD_OK) break;
+    const int mb = max_block_nlist(w);
+    for (int b = 32 * block_stride; b <= std::min(1024, mb); b += 32 * block_stride) {
+      if (b < w) continue;
+      const float t = median_time([&] { return launch_nlist(s->a, Launch{b, w}, 1, st); });
+      if (t < 0) { cudaGetLastError(); continue; }
+      if (t < best_t) { best_t = t; best_nl = Launch{b, w}; }
+    }
+  }
+  s->tune[MD_KERNEL_NLIST] = best_nl;
+  if (result == MD_OK && launch_nlist(s->a, best_nl, 1, st) != cudaSuccess) result = MD_ERR_CUDA;
+  if (result == MD_OK && launch_pair_span(s->a, best_pair, 0, s->span_pair, st) != cudaSuccess) result = MD_ERR_CUDA;
+  if (result == MD_OK && s->n_bonds > 0 && launch_bonds(s->a, 0, st) != cudaSuccess) result = MD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) result = MD_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->gvalid = false;
+  return result;
+}
+
+md_status md_set_step(md_system *s, int64_t step, md_stream stream) {
+  if (!s || step < 0) return MD_ERR_INVALID_ARG;
+  MD_CUDA(launch_set_step(s->a, step, reinterpret_cast<cudaStream_t>(stream)));
+  s->step = step;
+  return MD_OK;
+}
+
+md_status md_get_step(md_system *s, int64_t *step) {
+  if (!s || !step) return MD_ERR_INVALID_ARG;
+  MD_CUDA(cudaDeviceSynchronize());
+  MD_CUDA(cudaMemcpy(step, &s->a.ds->step, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  return MD_OK;
+}
+
+md_status md_poll_error(md_system *s, int64_t *detail) {
+  if (!s) return MD_ERR_INVALID_ARG;
+  if (detail) *detail = 0;
+  MD_CUDA(cudaDeviceSynchronize());
+  DevState ds;
+  MD_CUDA(cudaMemcpy(&ds, s->a.ds, sizeof(ds), cudaMemcpyDeviceToHost));
+  if (ds.error & kErrNlistOverflow) {
+    if (detail) *detail = ds.need_max_nb;
+    return MD_ERR_NLIST_OVERFLOW;
+  }
+  if (ds.error & kErrNonfinite) {
+    if (detail) *detail = ds.error_detail;
+    return MD_ERR_NONFINITE;
+  }
+  if (ds.error & kErrCellOverflow) return MD_ERR_CELL_OVERFLOW;
+  return MD_OK;
+}
+
+md_status md_get_forces(md_system *s, double *dev_force, double *dev_virial, md_stream stream) {
+  if (!s || !dev_force) return MD_ERR_INVALID_ARG;
+  MD_CUDA(launch_export_forces(s->a, dev_force, dev_virial, reinterpret_cast<cudaStream_t>(stream)));
+  return MD_OK;
+}
+
+md_status md_get_nlist(md_system *s, int32_t *dev_counts, int32_t *dev_rows, md_stream stream) {
+  if (!s || !dev_counts || !dev_rows) return MD_ERR_INVALID_ARG;
+  MD_CUDA(launch_export_nlist(s->a, dev_counts, dev_rows, reinterpret_cast<cudaStream_t>(stream)));
+  return MD_OK;
+}
+
+md_status md_get_cells(md_system *s, int32_t *dev_start, int32_t *dev_count, int32_t *dev_idx,
+                       md_stream stream) {
+  if (!s || !dev_start || !dev_count || !dev_idx) return MD_ERR_INVALID_ARG;
+  MD_CUDA(launch_export_cells(s->a, dev_start, dev_count, dev_idx, reinterpret_cast<cudaStream_t>(stream)));
+  return MD_OK;
+}
+
+md_status md_get_info(md_system *s, int64_t *n_cells, int32_t *max_nb, int64_t *n_builds) {
+  if (!s) return MD_ERR_INVALID_ARG;
+  if (n_cells) *n_cells = s->a.n_cells;
+  if (max_nb) *max_nb = s->a.max_nb;
+  if (n_builds) {
+    MD_CUDA(cudaDeviceSynchronize());
+    MD_CUDA(cudaMemcpy(n_builds, &s->a.ds->n_builds, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  }
+  return MD_OK;
+}
+
+md_status md_philox4x32_10(const uint32_t *dev_in, uint32_t *dev_out, int64_t n, md_stream stream) {
+  if (n < 0 || (n > 0 && (!dev_in || !dev_out))) return MD_ERR_INVALID_ARG;
+  MD_CUDA(launch_philox(dev_in, dev_out, n, reinterpret_cast<cudaStream_t>(stream)));
+  return MD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,404 @@
+// Velocity-Verlet integration with the fused half-buffer rebuild check,
+// harmonic bonds, thermo reductions and small utility kernels.
+#include "md_internal.cuh"
+
+namespace mdgb {
+
+namespace {
+
+inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+__device__ __forceinline__ double4 ld_force(const KArgs &a, int64_t i) {
+  if (a.mixed) {
+    float4 f = reinterpret_cast<const float4 *>(a.force)[i];
+    return make_double4(f.x, f.y, f.z, f.w);
+  }
+  return ld_d4(reinterpret_cast<const double4 *>(a.force) + i);
+}
+
+__device__ __forceinline__ double4 ld_d4_plain(const double4 *p) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+  double2 x = q[0], y = q[1];
+  return make_double4(x.x, x.y, y.x, y.y);
+}
+
+__device__ __forceinline__ void st_d4(double4 *p, const double4 &v) {
+  double2 *q = reinterpret_cast<double2 *>(p);
+  q[0] = make_double2(v.x, v.y);
+  q[1] = make_double2(v.z, v.w);
+}
+
+// One coordinate of the first velocity-Verlet half (Sec. 3): kick, drift and
+// wrap into [0, L) counting image crossings; same operation order as the
+// oracle (no fused multiply-add).
+// A crossing moves x by k L with k = floor(x / L) (k = +-1 for any sane time
+// step, where this equals the oracle's single subtraction); the fix-ups
+// absorb rounding at the box edge.  Non-finite x is left alone (and flagged
+// by the caller), so no loop depends on the value of x.
+__device__ __forceinline__ void kick_drift(double &x, double &v, int &img, double f, double hk,
+                                           double dt, double L) {
+  v = __dadd_rn(v, __dmul_rn(hk, f));
+  x = __dadd_rn(x, __dmul_rn(dt, v));
+  if ((x >= L || x < 0.0) && isfinite(x)) {
+    double k = floor(x / L);
+    k = fmin(fmax(k, -1e9), 1e9);
+    x = __dsub_rn(x, __dmul_rn(k, L));
+    img += (int)k;
+    if (x >= L) { x = __dsub_rn(x, L); img++; }
+    if (x < 0.0) { x = __dadd_rn(x, L); img--; }
+  }
+}
+
+// Velocity Verlet, first half, fused with the frame refresh of the FP32
+// positions and the rebuild check of Sec. 4.2 (a particle moved more than half
+// the buffer since the last build -> raise the replica's flag).  The last
+// block to finish advances the step counter and decides the sorts.
+__global__ void k_integrate1(KArgs a) {
+  __shared__ int is_last;
+  const int64_t t = a.ds->step;
+  const int par = (int)((t + 1) & 1);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) {
+    const int r = replica_of(a, i);
+    const Rep &rp = a.rep[r];
+    double4 x = ld_d4_plain(a.pos + i);
+    double4 v = ld_d4_plain(a.vel + i);
+    const double4 f = ld_force(a, i);
+    int4 img = a.image[i];
+    const int4 img0 = img;
+    const double hk = 0.5 * a.dt / a.mass;
+    kick_drift(x.x, v.x, img.x, f.x, hk, a.dt, rp.L[0]);
+    kick_drift(x.y, v.y, img.y, f.y, hk, a.dt, rp.L[1]);
+    kick_drift(x.z, v.z, img.z, f.z, hk, a.dt, rp.L[2]);
+    st_d4(a.pos + i, x);
+    st_d4(a.vel + i, v);
+    if (img.x != img0.x || img.y != img0.y || img.z != img0.z) a.image[i] = img;
+    float4 o = a.pos4f[i];
+    const uint32_t w = __float_as_uint(o.w);
+    o.x = frame_offset(x.x, cell_x(w), rp.h[0], rp.L[0]);
+    o.y = frame_offset(x.y, cell_y(w), rp.h[1], rp.L[1]);
+    o.z = frame_offset(x.z, cell_z(w), rp.h[2], rp.L[2]);
+    a.pos4f[i] = o;
+    const float4 ref = a.oref[i];
+    const float ex = o.x - ref.x, ey = o.y - ref.y, ez = o.z - ref.z;
+    const float d2 = ex * ex + ey * ey + ez * ez;
+    if (!(d2 <= a.disp2_f)) a.rebuild[2 * r + par] = 1;  // NaN also triggers
+    if (!isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z)) {
+      if (atomicOr(&a.ds->error, kErrNonfinite) == 0u) a.ds->error_detail = i;
+    }
+    if (a.vel4f) a.vel4f[i] = make_float4((float)v.x, (float)v.y, (float)v.z, __int_as_float(a.tag[i]));
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(&a.ds->blocks_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int r = threadIdx.x; r < a.R; r += blockDim.x) {
+    const int rb = __ldcg(a.rebuild + 2 * r + par);
+    int now = 0;
+    if (a.sort_period > 0 && rb && (t + 1 - __ldcg(a.last_sort + r)) >= a.sort_period) {
+      now = 1;
+      a.last_sort[r] = t + 1;
+    }
+    a.sort_now[r] = now;
+    a.rebuild[2 * r + (int)(t & 1)] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.ds->blocks_done = 0u;
+    a.ds->step = t + 1;
+  }
+}
+
+// Velocity Verlet, second half: v += dt/2 F/m.
+__global__ void k_integrate2(KArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  double4 v = ld_d4_plain(a.vel + i);
+  const double4 f = ld_force(a, i);
+  const double hk = 0.5 * a.dt / a.mass;
+  v.x = __dadd_rn(v.x, __dmul_rn(hk, f.x));
+  v.y = __dadd_rn(v.y, __dmul_rn(hk, f.y));
+  v.z = __dadd_rn(v.z, __dmul_rn(hk, f.z));
+  st_d4(a.vel + i, v);
+}
+
+// Harmonic bonds (Sec. 4.3.4: a bond is an unordered pair of particle IDs):
+// each particle sums the bonds it belongs to, so no atomics are needed.
+// V = K/2 (r - r0)^2, F_i = -K (r - r0) (x_i - x_j) / r.
+template <bool ENERGY>
+__global__ void k_bonds(KArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int r = replica_of(a, i);
+  const Rep &rp = a.rep[r];
+  const int32_t ti = a.tag[i];
+  const double4 pi = ld_d4(a.pos + i);
+  double f[3] = {0., 0., 0.}, pe = 0., w[6] = {0., 0., 0., 0., 0., 0.};
+  bool any = false;
+  for (int b = 0; b < a.max_bonds; b++) {
+    const int32_t p = a.btab[(int64_t)ti * a.max_bonds + b];
+    if (p < 0) break;
+    any = true;
+    const int32_t j = a.rtag[p];
+    double d[3];
+    const double r2 = exact_r2(pi, ld_d4(a.pos + j), rp, d);
+    double fr, dr;
+    if (a.bond_r0 == 0.0) {
+      fr = -a.bond_K;
+      dr = sqrt(r2);
+    } else {
+      dr = sqrt(r2);
+      fr = dr > 0.0 ? -a.bond_K * (dr - a.bond_r0) / dr : 0.0;
+    }
+    const double fx = fr * d[0], fy = fr * d[1], fz = fr * d[2];
+    f[0] += fx; f[1] += fy; f[2] += fz;
+    if (ENERGY) {
+      pe += 0.25 * a.bond_K * (dr - a.bond_r0) * (dr - a.bond_r0);
+      w[0] += 0.5 * d[0] * fx; w[1] += 0.5 * d[0] * fy; w[2] += 0.5 * d[0] * fz;
+      w[3] += 0.5 * d[1] * fy; w[4] += 0.5 * d[1] * fz; w[5] += 0.5 * d[2] * fz;
+    }
+  }
+  if (!any) return;
+  if (a.mixed) {
+    float4 *F = reinterpret_cast<float4 *>(a.force) + i;
+    float4 g = *F;
+    g.x += (float)f[0]; g.y += (float)f[1]; g.z += (float)f[2];
+    if (ENERGY) g.w += (float)pe;
+    *F = g;
+    if (ENERGY) {
+      float *vv = reinterpret_cast<float *>(a.virial) + 6 * i;
+      for (int c = 0; c < 6; c++) vv[c] += (float)w[c];
+    }
+  } else {
+    double4 *F = reinterpret_cast<double4 *>(a.force) + i;
+    double4 g = ld_d4_plain(F);
+    g.x += f[0]; g.y += f[1]; g.z += f[2];
+    if (ENERGY) g.w += pe;
+    st_d4(F, g);
+    if (ENERGY) {
+      double *vv = reinterpret_cast<double *>(a.virial) + 6 * i;
+      for (int c = 0; c < 6; c++) vv[c] += w[c];
+    }
+  }
+}
+
+// Thermo reduction, stage 1: one block per chunk of <= kThermoChunk particles
+// of one replica.  Fixed assignment of particles to threads and a fixed
+// shared-memory tree: the result is bitwise reproducible.
+__global__ void __launch_bounds__(256) k_thermo_part(KArgs a) {
+  __shared__ double sh[8][256];
+  const int64_t ch = blockIdx.x;
+  const int r = a.tchunk_rep[ch];
+  const Rep &rp = a.rep[r];
+  const int64_t p0 = rp.p0 + (ch - rp.tchunk0) * kThermoChunk;
+  const int64_t p1 = min(p0 + kThermoChunk, rp.p1);
+  double acc[8] = {0., 0., 0., 0., 0., 0., 0., 0.};  // ke, pe, w, px, py, pz
+  for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+    const double4 v = ld_d4(a.vel + i);
+    const double4 f = ld_force(a, i);
+    acc[0] += 0.5 * a.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
+    acc[1] += f.w;
+    if (a.mixed) {
+      const float *vv = reinterpret_cast<const float *>(a.virial) + 6 * i;
+      acc[2] += (double)vv[0] + (double)vv[3] + (double)vv[5];
+    } else {
+      const double *vv = reinterpret_cast<const double *>(a.virial) + 6 * i;
+      acc[2] += vv[0] + vv[3] + vv[5];
+    }
+    acc[3] += a.mass * v.x;
+    acc[4] += a.mass * v.y;
+    acc[5] += a.mass * v.z;
+  }
+  for (int k = 0; k < 8; k++) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < 6; k++) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) a.tpart[ch * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// Stage 2: one thread per replica sums its chunks in order and derives
+// P = (2 KE + W) / (3 V) and T = 2 KE / (3 N - 3).
+__global__ void k_thermo_final(KArgs a, double *out, int from_run) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= a.R) return;
+  const Rep &rp = a.rep[r];
+  double s[6] = {0., 0., 0., 0., 0., 0.};
+  for (int c = 0; c < rp.ntchunk; c++)
+    for (int k = 0; k < 6; k++) s[k] += a.tpart[(rp.tchunk0 + c) * 8 + k];
+  double *o = out;
+  if (from_run) {
+    // row = number of multiples of the period in (run_base, step], minus one
+    const DevState *ds = a.ds;
+    if (ds->thermo_out == nullptr) return;
+    const int64_t p = ds->thermo_period;
+    const int64_t row = ds->step / p - ds->run_base / p - 1;
+    if (row < 0 || row >= ds->thermo_rows) return;
+    o = ds->thermo_out + row * (int64_t)a.R * 8;
+  }
+  const double n = (double)(rp.p1 - rp.p0);
+  double *q = o + 8 * r;
+  q[0] = s[0];
+  q[1] = s[1];
+  q[2] = s[2];
+  q[3] = (2.0 * s[0] + s[2]) / (3.0 * rp.volume);
+  q[4] = n > 1.0 ? 2.0 * s[0] / (3.0 * n - 3.0) : 0.0;
+  q[5] = s[3];
+  q[6] = s[4];
+  q[7] = s[5];
+}
+
+// Frames of the FP32 positions from the current FP64 positions, without
+// building cells (used once at creation so that md_integrate is defined
+// before the first build).
+__global__ void k_init_frames(KArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const Rep &rp = a.rep[replica_of(a, i)];
+  const double4 x = ld_d4(a.pos + i);
+  const int cx = cell_coord(x.x, rp.inv_h[0], rp.nc[0]);
+  const int cy = cell_coord(x.y, rp.inv_h[1], rp.nc[1]);
+  const int cz = cell_coord(x.z, rp.inv_h[2], rp.nc[2]);
+  float4 o;
+  o.x = frame_offset(x.x, cx, rp.h[0], rp.L[0]);
+  o.y = frame_offset(x.y, cy, rp.h[1], rp.L[1]);
+  o.z = frame_offset(x.z, cz, rp.h[2], rp.L[2]);
+  // tags must be a permutation of 0..N-1 and types lie in [0, ntypes): both
+  // index tables later, so out-of-range values are refused here
+  const int32_t tg = a.tag[i], ty = a.type[i];
+  const bool ok = tg >= 0 && tg < a.n && ty >= 0 && ty < a.ntypes;
+  if (!ok) set_error(a.ds, kErrBadInput);
+  o.w = __uint_as_float(pack_cell(cx, cy, cz, ok ? ty : 0));
+  a.pos4f[i] = o;
+  a.oref[i] = o;
+  a.cell_idx[i] = (int32_t)i;
+  if (ok) a.rtag[tg] = (int32_t)i;
+  if (a.vel4f) {
+    const double4 v = ld_d4(a.vel + i);
+    a.vel4f[i] = make_float4((float)v.x, (float)v.y, (float)v.z, __int_as_float(a.tag[i]));
+  }
+}
+
+__global__ void k_set_step(KArgs a, int64_t step) { a.ds->step = step; }
+
+__global__ void k_run_begin(KArgs a, double *out, int64_t period, int64_t rows) {
+  a.ds->run_base = a.ds->step;
+  a.ds->thermo_out = out;
+  a.ds->thermo_period = period > 0 ? period : 1;
+  a.ds->thermo_rows = rows;
+}
+
+__global__ void k_export_forces(KArgs a, double *f, double *v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const double4 g = ld_force(a, i);
+  f[4 * i] = g.x; f[4 * i + 1] = g.y; f[4 * i + 2] = g.z; f[4 * i + 3] = g.w;
+  if (v) {
+    for (int c = 0; c < 6; c++)
+      v[6 * i + c] = a.mixed ? (double)reinterpret_cast<const float *>(a.virial)[6 * i + c]
+                             : reinterpret_cast<const double *>(a.virial)[6 * i + c];
+  }
+}
+
+__global__ void k_export_nlist(KArgs a, int32_t *counts, int32_t *rows) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int nn = a.n_nb[i];
+  counts[i] = nn;
+  for (int k = 0; k < a.max_nb; k++)
+    rows[i * a.max_nb + k] =
+        k < nn ? (int32_t)(a.nl[nl_addr(i, k, a.w_store_log2, a.n_pad)] & kIdxMask) : -1;
+}
+
+__global__ void k_export_cells(KArgs a, int32_t *start, int32_t *count, int32_t *idx) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n_cells) {
+    start[i] = a.cell_start[i];
+    count[i] = a.cell_count[i];
+  }
+  if (i < a.n) idx[i] = a.cell_idx[i];
+}
+
+__global__ void k_philox(const uint32_t *in, uint32_t *out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t *q = in + 6 * i;
+  U4 c = philox4x32_10(U4{q[0], q[1], q[2], q[3]}, q[4], q[5]);
+  out[4 * i] = c.x; out[4 * i + 1] = c.y; out[4 * i + 2] = c.z; out[4 * i + 3] = c.w;
+}
+
+}  // namespace
+
+cudaError_t launch_integrate1(const KArgs &a, cudaStream_t st) {
+  // the step counter must advance even for an empty system
+  k_integrate1<<<blocks_for(a.n > 0 ? a.n : 1, 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integrate2(const KArgs &a, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  k_integrate2<<<blocks_for(a.n, 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bonds(const KArgs &a, int want_virial, cudaStream_t st) {
+  if (a.n == 0 || a.max_bonds == 0) return cudaSuccess;
+  if (want_virial) k_bonds<true><<<blocks_for(a.n, 256), 256, 0, st>>>(a);
+  else k_bonds<false><<<blocks_for(a.n, 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thermo(const KArgs &a, double *out, int from_run, cudaStream_t st) {
+  if (a.n_tchunks > 0) k_thermo_part<<<(unsigned)a.n_tchunks, 256, 0, st>>>(a);
+  k_thermo_final<<<blocks_for(a.R, 64), 64, 0, st>>>(a, out, from_run);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_step(const KArgs &a, int64_t step, cudaStream_t st) {
+  k_set_step<<<1, 1, 0, st>>>(a, step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_run_begin(const KArgs &a, double *out, int64_t period, int64_t rows,
+                             cudaStream_t st) {
+  k_run_begin<<<1, 1, 0, st>>>(a, out, period, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_frames(const KArgs &a, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  k_init_frames<<<blocks_for(a.n, 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_forces(const KArgs &a, double *f, double *v, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  k_export_forces<<<blocks_for(a.n, 256), 256, 0, st>>>(a, f, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_nlist(const KArgs &a, int32_t *counts, int32_t *rows, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  k_export_nlist<<<blocks_for(a.n, 256), 256, 0, st>>>(a, counts, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_cells(const KArgs &a, int32_t *start, int32_t *count, int32_t *idx,
+                                cudaStream_t st) {
+  int64_t m = a.n_cells > a.n ? a.n_cells : a.n;
+  if (m == 0) return cudaSuccess;
+  k_export_cells<<<blocks_for(m, 256), 256, 0, st>>>(a, start, count, idx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_philox<<<blocks_for(n, 256), 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace mdgb

@@ -1,0 +1,245 @@
+// Internal definitions shared by the CUDA translation units of libmdgb.
+// Not part of the public ABI (include/md.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/md.h"
+
+namespace mdgb {
+
+constexpr int kMaxTypes = 32;
+constexpr int kChunkCells = 2048;     // cells per scan chunk (256 threads x 8)
+constexpr int kThermoChunk = 4096;    // particles per thermo partial sum
+constexpr int kIdxBits = 27;          // neighbour entry: index bits, code in the top 5
+constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
+constexpr int kMaxCellSort = 256;     // largest cell the in-cell sort handles
+constexpr int kCellBits = 9;          // packed cell coordinate bits (nc <= 512)
+constexpr int64_t kMaxParticles = (int64_t)1 << kIdxBits;
+
+// Device error word bits.
+enum : uint32_t {
+  kErrNlistOverflow = 1u << 0,
+  kErrNonfinite = 1u << 1,
+  kErrCellOverflow = 1u << 2,
+  kErrBadInput = 1u << 3,
+};
+
+// Per-replica constants (device-resident copy + host mirror).
+struct Rep {
+  int64_t p0, p1;     // particle range [p0, p1)
+  int64_t cell0;      // first cell slot (chunk aligned) in the cell arrays
+  int64_t chunk0;     // first scan chunk
+  int64_t tchunk0;    // first thermo chunk
+  int32_t nc[3];      // cells per edge
+  int32_t ncell;      // nc0 nc1 nc2
+  int32_t nchunk;     // scan chunks
+  int32_t ntchunk;    // thermo chunks
+  double L[3];
+  double inv_L[3];
+  double h[3];        // L / nc
+  double inv_h[3];    // nc / L
+  float hf[3];        // float(h): shift of a neighbouring cell's frame
+  float band;         // FP32 r^2 uncertainty band (see DESIGN: exact decisions)
+  double volume;
+};
+
+// Global device state (one per system, in the workspace).
+struct DevState {
+  int64_t step;          // time step of the current positions
+  int64_t run_base;      // md_run: step before the first step of the run
+  double *thermo_out;    // md_run: device output rows (or null)
+  int64_t thermo_period;
+  uint32_t error;        // OR of kErr* bits
+  int32_t need_max_nb;   // largest row seen when overflowing
+  int64_t error_detail;  // particle index of the first non-finite position
+  uint32_t blocks_done;  // integrate(1) last-block ticket
+  uint32_t pad0;
+  int64_t n_builds;      // replica list builds so far
+  int64_t thermo_rows;   // md_run: capacity of thermo_out in rows
+};
+
+// Pair coefficients, prepared on the host.
+struct LJCoeffD { double lj1, lj2, lj3, lj4, vshift, pad0, pad1, pad2; };  // 64 B
+struct LJCoeffF { float lj1, lj2, lj3, lj4, vshift, pad0, pad1, pad2; };
+struct DPDCoeffD { double A, gamma, sigma_rdt, pad; };  // sigma / sqrt(dt)
+struct DPDCoeffF { float A, gamma, sigma_rdt, pad; };
+
+// Everything a kernel needs, passed by value (< 4 KB).
+struct KArgs {
+  int64_t n;           // particles
+  int64_t n_pad;       // padded particle count (list pitch)
+  int32_t R;
+  int32_t ntypes;
+  const int64_t *rep_off;  // [R+1]
+  const Rep *rep;          // [R]
+  const int32_t *chunk_rep;   // [n chunks] replica of each scan chunk
+  const int32_t *tchunk_rep;  // [n thermo chunks]
+  // caller state
+  double4 *pos;
+  double4 *vel;
+  int4 *image;
+  int32_t *tag;
+  int32_t *type;
+  // internal
+  float4 *pos4f;       // frame-relative FP32 position, packed frame cell + type
+  float4 *oref;        // frame-relative position at the last build
+  float4 *vel4f;       // FP32 velocity, tag bits in w (DPD mixed)
+  int32_t *cell_rank;  // [cells] linear cell -> Hilbert rank (per replica)
+  int32_t *cell_count; // [cells]
+  int32_t *cell_start; // [cells] first particle (global index)
+  int32_t *chunk_sum;  // [chunks]
+  int32_t *cell_idx;   // [N]
+  int32_t *pcell;      // [N] cell slot of each particle (binning)
+  int32_t *pslot;      // [N] rank inside its cell (binning)
+  uint32_t *nl;        // [max_nb * n_pad]
+  int32_t *n_nb;       // [N]
+  void *force;         // double4[N] (FP64) or float4[N] (mixed)
+  void *virial;        // double[N][6] or float[N][6]
+  double *tpart;       // [thermo chunks][8]
+  DevState *ds;
+  int32_t *rebuild;    // [R][2]
+  int32_t *sort_now;   // [R]
+  int64_t *last_sort;  // [R]
+  int32_t *rtag;       // [N] tag -> index
+  int32_t *btab;       // [N][max_bonds] partner tags (-1 = none)
+  // sort scratch
+  double4 *s_pos, *s_vel;
+  int4 *s_img;
+  int32_t *s_tag, *s_type;
+  float4 *s_pos4f, *s_oref, *s_vel4f;
+  const void *coeff;   // LJCoeff* / DPDCoeff* [ntypes^2], precision-matched
+  // parameters
+  int32_t max_nb;
+  int32_t w_store_log2;  // neighbour-list tile width (pair kernel's w)
+  int32_t sort_period;
+  int32_t max_bonds;
+  int32_t mixed;
+  int32_t pair;
+  double r_cut, rc2, rl2;
+  float rc2f, rl2f;
+  double dt, mass, kT;
+  double bond_K, bond_r0;
+  float disp2_f;       // (r_skin / 2)^2, slightly reduced
+  uint64_t seed;
+  int64_t n_chunks, n_tchunks, n_cells;
+};
+
+// ---- device helpers -------------------------------------------------------
+
+__device__ __forceinline__ int replica_of(const KArgs &a, int64_t i) {
+  if (a.R == 1) return 0;
+  int lo = 0, hi = a.R - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(a.rep_off + mid) <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t pack_cell(int cx, int cy, int cz, int type) {
+  return (uint32_t)cx | ((uint32_t)cy << kCellBits) | ((uint32_t)cz << (2 * kCellBits)) |
+         ((uint32_t)type << (3 * kCellBits));
+}
+__device__ __forceinline__ int cell_x(uint32_t w) { return (int)(w & 511u); }
+__device__ __forceinline__ int cell_y(uint32_t w) { return (int)((w >> kCellBits) & 511u); }
+__device__ __forceinline__ int cell_z(uint32_t w) { return (int)((w >> (2 * kCellBits)) & 511u); }
+__device__ __forceinline__ int cell_type(uint32_t w) { return (int)(w >> (3 * kCellBits)); }
+
+// Cell coordinate exactly as floor(x * (nc / L)) clamped to [0, nc).
+__device__ __forceinline__ int cell_coord(double x, double inv_h, int nc) {
+  int c = (int)floor(__dmul_rn(x, inv_h));
+  c = c >= nc ? nc - 1 : c;
+  return c < 0 ? 0 : c;
+}
+
+// FP32 offset of x from the centre of frame cell c, folded into (-L/2, L/2].
+__device__ __forceinline__ float frame_offset(double x, int c, double h, double L) {
+  double d = x - ((double)c + 0.5) * h;
+  if (d > 0.5 * L) d -= L;
+  else if (d < -0.5 * L) d += L;
+  return (float)d;
+}
+
+// Exact FP64 minimum-image r^2 with a fixed operation order and no FMA:
+// dx = (x_i - x_j) - L rint((x_i - x_j) / L); r2 = (dx dx + dy dy) + dz dz.
+__device__ __forceinline__ double exact_r2(const double4 &pi, const double4 &pj, const Rep &rp,
+                                           double *d) {
+  double dx = __dsub_rn(pi.x, pj.x);
+  double dy = __dsub_rn(pi.y, pj.y);
+  double dz = __dsub_rn(pi.z, pj.z);
+  dx = __dsub_rn(dx, __dmul_rn(rp.L[0], rint(__dmul_rn(dx, rp.inv_L[0]))));
+  dy = __dsub_rn(dy, __dmul_rn(rp.L[1], rint(__dmul_rn(dy, rp.inv_L[1]))));
+  dz = __dsub_rn(dz, __dmul_rn(rp.L[2], rint(__dmul_rn(dz, rp.inv_L[2]))));
+  d[0] = dx; d[1] = dy; d[2] = dz;
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__device__ __forceinline__ double4 ld_d4(const double4 *p) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+  double2 a = __ldg(q), b = __ldg(q + 1);
+  return make_double4(a.x, a.y, b.x, b.y);
+}
+
+// Neighbour-list address of entry k of row i for tile width 2^lw.
+__device__ __forceinline__ size_t nl_addr(int64_t i, int k, int lw, int64_t n_pad) {
+  return ((((size_t)(k >> lw)) * (size_t)n_pad + (size_t)i) << lw) | (size_t)(k & ((1 << lw) - 1));
+}
+
+__device__ __forceinline__ void set_error(DevState *ds, uint32_t bit) { atomicOr(&ds->error, bit); }
+
+// ---- Philox-4x32-10 (Salmon et al., SC'11) --------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    U4 n;
+    n.x = hi1 ^ c.y ^ k0;
+    n.y = lo1;
+    n.z = hi0 ^ c.w ^ k1;
+    n.w = lo0;
+    c = n;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t dpd_word(int32_t ti, int32_t tj, uint64_t step, uint64_t seed) {
+  uint32_t a = (uint32_t)ti, b = (uint32_t)tj;
+  U4 c{a < b ? a : b, a < b ? b : a, (uint32_t)step, (uint32_t)(step >> 32)};
+  return philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32)).x;
+}
+
+// ---- launch wrappers (defined in the k_*.cu files) ------------------------
+struct Launch { int block; int w; };
+
+cudaError_t launch_integrate1(const KArgs &a, cudaStream_t st);
+cudaError_t launch_integrate2(const KArgs &a, cudaStream_t st);
+cudaError_t launch_bin(const KArgs &a, int force, cudaStream_t st);
+cudaError_t launch_sort(const KArgs &a, int force, cudaStream_t st);
+cudaError_t launch_nlist(const KArgs &a, Launch l, int force, cudaStream_t st);
+cudaError_t launch_pair_span(const KArgs &a, Launch l, int want_virial, int span, cudaStream_t st);
+int pair_span(const int64_t *off, int R, int64_t n, int per_block);
+cudaError_t launch_bonds(const KArgs &a, int want_virial, cudaStream_t st);
+cudaError_t launch_thermo(const KArgs &a, double *out, int from_run, cudaStream_t st);
+cudaError_t launch_set_step(const KArgs &a, int64_t step, cudaStream_t st);
+cudaError_t launch_run_begin(const KArgs &a, double *out, int64_t period, int64_t rows,
+                             cudaStream_t st);
+cudaError_t launch_clear_state(const KArgs &a, cudaStream_t st);
+cudaError_t launch_force_rebuild_flags(const KArgs &a, cudaStream_t st);
+cudaError_t launch_export_forces(const KArgs &a, double *f, double *v, cudaStream_t st);
+cudaError_t launch_export_nlist(const KArgs &a, int32_t *counts, int32_t *rows, cudaStream_t st);
+cudaError_t launch_export_cells(const KArgs &a, int32_t *start, int32_t *count, int32_t *idx,
+                                cudaStream_t st);
+cudaError_t launch_philox(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t st);
+cudaError_t launch_init_frames(const KArgs &a, cudaStream_t st);
+int max_block_nlist(int w);
+int max_block_pair(const KArgs &a, int w, int want_virial);
+
+}  // namespace mdgb

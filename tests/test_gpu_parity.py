@@ -1,0 +1,400 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the CPU oracle
+on the same seeded inputs.  Sizes span several blocks and end in ragged
+tails.  Tolerances:
+  * neighbour rows, cells, sort order, Philox words: bit-exact;
+  * FP64 forces: |dF| <= 1e-12 |F| where |F| >= 1e-2 S, else |dF| <= 1e-14 S
+    (S = sum_j |f_ij|; summation order differs between the two sides);
+  * mixed forces: RMS relative error <= 1e-5, max <= 1e-3 over particles with
+    |F| >= 1e-2 S.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_3387_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1412_3387_gb300 import md  # noqa: E402
+
+WS = (1, 2, 4, 8, 16, 32)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1412_3387_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def fp64_force_check(f_gpu, f_ref, absf, what=""):
+    d = np.linalg.norm(f_gpu[:, :3] - f_ref[:, :3], axis=1)
+    F = np.linalg.norm(f_ref[:, :3], axis=1)
+    big = F >= 1e-2 * absf
+    assert np.all(d[big] <= 1e-12 * F[big]), (what, np.max(d[big] / F[big]))
+    assert np.all(d[~big] <= 1e-14 * absf[~big] + 1e-300), what
+
+
+def mixed_force_stats(f_gpu, f_ref, absf):
+    d = np.linalg.norm(f_gpu[:, :3] - f_ref[:, :3], axis=1)
+    F = np.linalg.norm(f_ref[:, :3], axis=1)
+    big = F >= 1e-2 * absf
+    rel = d[big] / F[big]
+    return float(np.sqrt(np.mean(rel ** 2))), float(rel.max())
+
+
+def lj_state(n=4000, rho=0.8442, T=1.44, seed=21, jitter=0.12):
+    return inputs.lj_fluid(n, rho, T, seed=seed, jitter=jitter)
+
+
+_EQ_CACHE = {}
+
+
+def equilibrated_lj(n=4000, rho=0.8442, T=1.2, seed=3, steps=600, r_skin=0.3):
+    """A liquid snapshot produced by the oracle (never by the CUDA path)."""
+    key = (n, rho, T, seed, steps, r_skin)
+    if key not in _EQ_CACHE:
+        st = inputs.lj_fluid(n, rho, T, seed=seed)
+        out = oracle.run(st.pos, st.vel, st.image, st.box[0], steps, r_cut=2.5,
+                         r_skin=r_skin, dt=0.005)
+        s2 = st.copy()
+        s2.pos, s2.vel, s2.image = out["pos"], out["vel"], out["image"]
+        _EQ_CACHE[key] = s2
+    return _EQ_CACHE[key].copy()
+
+
+# --------------------------------------------------------------------------
+
+def test_philox_bitwise_equal_to_oracle():
+    rng = np.random.default_rng(5)
+    rows = rng.integers(0, 2 ** 32, (3000, 6), dtype=np.uint64).astype(np.uint32)
+    rows[0] = 0
+    rows[1] = 0xFFFFFFFF
+    got = md.philox4x32_10(rows)
+    for k in range(rows.shape[0]):
+        assert got[k].tolist() == oracle.philox4x32_10(rows[k, :4], rows[k, 4:]).tolist()
+
+
+@pytest.mark.parametrize("w", WS)
+def test_nlist_rows_equal_brute_force(w):
+    st = lj_state(n=3001)
+    L = st.box[0, 0]
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005)
+    s.set_tuning(md.KERNEL_PAIR, 128, w)
+    s.set_tuning(md.KERNEL_NLIST, 64 if w < 32 else 128, w)
+    s.build_cells()
+    s.build_nlist()
+    counts, rows = (x.cpu().numpy() for x in s.nlist())
+    s.check_error()
+    cb, rb = oracle.neighbors(st.pos, L, 2.8, max_nb=s.max_nb, method="brute")
+    assert np.array_equal(counts, cb)
+    for i in range(st.n):
+        assert np.array_equal(np.sort(rows[i, :counts[i]]), rb[i, :cb[i]]), i
+    assert np.all(rows[np.arange(s.max_nb)[None, :] >= counts[:, None]] == -1)
+
+
+def test_nlist_dpd_density_and_tiny_box():
+    st = inputs.dpd_fluid(2500, 3.0, 1.0, seed=9)
+    s = md.MDSystem(st, r_cut=1.0, r_skin=0.3, dt=0.02, pair="dpd", coeff=[[25.0, 4.5]])
+    s.build_cells()
+    s.build_nlist()
+    counts, rows = (x.cpu().numpy() for x in s.nlist())
+    cb, rb = oracle.neighbors(st.pos, st.box[0], 1.3, max_nb=s.max_nb, method="brute")
+    assert np.array_equal(counts, cb)
+    for i in range(st.n):
+        assert np.array_equal(np.sort(rows[i, :counts[i]]), rb[i, :cb[i]])
+    # smallest legal box: exactly 3 cells per edge
+    st2 = inputs.lj_fluid(256, 0.8442, 1.0, seed=2, jitter=0.1)  # L = 6.72 -> 3 cells of 2.24
+    s2 = md.MDSystem(st2, r_cut=1.9, r_skin=0.3, dt=0.005)
+    s2.build_cells()
+    s2.build_nlist()
+    c2, r2 = (x.cpu().numpy() for x in s2.nlist())
+    cb2, rb2 = oracle.neighbors(st2.pos, st2.box[0], 2.2, max_nb=s2.max_nb, method="brute")
+    assert np.array_equal(c2, cb2)
+    for i in range(st2.n):
+        assert np.array_equal(np.sort(r2[i, :c2[i]]), rb2[i, :cb2[i]])
+
+
+def test_cells_bin_every_particle_in_order():
+    st = lj_state(n=5003)
+    L = st.box[0, 0]
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005)
+    s.build_cells()
+    start, count, idx = (x.cpu().numpy() for x in s.cells())
+    nc = oracle.cells_per_dim(L, 2.8)
+    cc = oracle.cell_coords(st.pos, L, [nc] * 3)
+    assert count.sum() == st.n
+    assert sorted(idx.tolist()) == list(range(st.n))
+    seen = np.zeros(st.n, bool)
+    occupied = np.nonzero(count)[0]
+    for c in occupied:
+        m = idx[start[c]:start[c] + count[c]]
+        assert np.all(np.diff(m) > 0)  # ascending index inside a cell
+        assert len({tuple(cc[j]) for j in m}) == 1
+        seen[m] = True
+    assert seen.all()
+    # cells are laid out contiguously in cell order
+    assert np.all(start[occupied][1:] == (start + count)[occupied][:-1])
+
+
+@pytest.mark.parametrize("w", (1, 4, 32))
+def test_lj_fp64_forces_match_oracle(w):
+    st = equilibrated_lj()
+    L = st.box[0]
+    ref, vref, absf = oracle.lj_forces(st.pos, L, 2.5)
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005)
+    s.set_tuning(md.KERNEL_PAIR, 256, w)
+    s.prepare()
+    s.compute_pair(want_virial=True)
+    f, v = (x.cpu().numpy() for x in s.forces(virial=True))
+    s.check_error()
+    fp64_force_check(f, ref, absf, f"w={w}")
+    assert np.allclose(f[:, 3], ref[:, 3], rtol=1e-12, atol=1e-12 * absf.max())
+    assert np.allclose(v, vref, rtol=1e-11, atol=1e-12 * absf.max())
+
+
+def test_lj_fp64_shifted_energy_and_multitype():
+    st = lj_state(n=2999, jitter=0.1)
+    t = (np.arange(st.n) * 7919 % 3).astype(np.int32)
+    st.type = t
+    coeff = np.array([[[1.0, 1.0], [0.8, 1.05], [0.5, 0.95]],
+                      [[0.8, 1.05], [1.5, 1.1], [1.2, 1.0]],
+                      [[0.5, 0.95], [1.2, 1.0], [0.9, 0.9]]])
+    ref, vref, absf = oracle.lj_forces(st.pos, st.box[0], 2.5, coeff=coeff, type=t,
+                                       shift_energy=True)
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, coeff=coeff, shift_energy=True)
+    s.prepare()
+    s.compute_pair(want_virial=True)
+    f = s.forces().cpu().numpy()
+    fp64_force_check(f, ref, absf)
+    assert np.allclose(f[:, 3], ref[:, 3], rtol=1e-12, atol=1e-12 * absf.max())
+
+
+@pytest.mark.parametrize("w", (1, 4, 16))
+def test_lj_mixed_forces_within_tolerance(w):
+    st = equilibrated_lj()
+    ref, vref, absf = oracle.lj_forces(st.pos, st.box[0], 2.5)
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, precision="mixed")
+    s.set_tuning(md.KERNEL_PAIR, 256, w)
+    s.prepare()
+    s.compute_pair(want_virial=True)
+    f, v = (x.cpu().numpy() for x in s.forces(virial=True))
+    rms, mx = mixed_force_stats(f, ref, absf)
+    assert rms <= 1e-5 and mx <= 1e-3, (rms, mx)
+    assert abs(f[:, 3].sum() - ref[:, 3].sum()) <= 1e-5 * np.abs(ref[:, 3]).sum()
+    assert abs(v[:, [0, 3, 5]].sum() - vref[:, [0, 3, 5]].sum()) <= 1e-5 * np.abs(vref).sum()
+
+
+@pytest.mark.parametrize("prec", ("fp64", "mixed"))
+def test_dpd_forces_match_oracle(prec):
+    st = inputs.dpd_fluid(3001, 3.0, 1.0, seed=31)
+    L = st.box[0]
+    step, seed = 12345, 0xDEADBEEF12
+    coeff = [[25.0, 4.5]]
+    ref, vref, absf = oracle.dpd_forces(st.pos, st.vel, L, 1.0, coeff, 1.0, 0.02, step, seed)
+    s = md.MDSystem(st, r_cut=1.0, r_skin=0.3, dt=0.02, pair="dpd", coeff=coeff, kT=1.0,
+                    seed=seed, precision=prec)
+    s.set_step(step)
+    s.prepare()
+    s.compute_pair(want_virial=True)
+    f = s.forces().cpu().numpy()
+    if prec == "fp64":
+        fp64_force_check(f, ref, absf)
+    else:
+        rms, mx = mixed_force_stats(f, ref, absf)
+        assert rms <= 1e-5 and mx <= 1e-3, (rms, mx)
+
+
+@pytest.mark.parametrize("prec", ("fp64", "mixed"))
+def test_diblock_bonds_and_dpd_match_oracle(prec):
+    st = inputs.diblock_melt(64, 32, 3.0, 1.0, seed=41)
+    L = st.box[0]
+    coeff = np.array([[[25.0, 4.5], [40.0, 4.5]], [[40.0, 4.5], [25.0, 4.5]]])
+    step, seed = 7, 99
+    ref, vref, absf = oracle.dpd_forces(st.pos, st.vel, L, 1.0, coeff, 1.0, 0.02, step, seed,
+                                        type=st.type)
+    ref, vref, absf = oracle.bond_forces(st.bonds, st.pos, L, 4.0, 0.0, ref, vref, absf)
+    s = md.MDSystem(st, r_cut=1.0, r_skin=0.3, dt=0.02, pair="dpd", coeff=coeff, kT=1.0,
+                    seed=seed, precision=prec, bond_K=4.0, bond_r0=0.0)
+    s.set_step(step)
+    s.prepare()
+    s.compute_forces(want_virial=True)
+    f, v = (x.cpu().numpy() for x in s.forces(virial=True))
+    if prec == "fp64":
+        fp64_force_check(f, ref, absf)
+        assert np.allclose(f[:, 3], ref[:, 3], rtol=1e-12, atol=1e-12 * absf.max())
+    else:
+        rms, mx = mixed_force_stats(f, ref, absf)
+        assert rms <= 1e-5 and mx <= 1e-3, (rms, mx)
+
+
+def test_fp64_trajectory_matches_oracle_100_steps():
+    st = lj_state(n=4000, T=1.44, jitter=0.0)
+    L = st.box[0]
+    out = oracle.run(st.pos, st.vel, st.image, L, 100, r_cut=2.5, r_skin=0.3, dt=0.005,
+                     shift_energy=True, thermo_period=10)
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, shift_energy=True, thermo_period=10)
+    s.prepare()
+    th = s.run_with_thermo(100).cpu().numpy()[:, 0, :]
+    s.check_error()
+    g = s.state_numpy()
+    # compare by tag (no sort here, so indices are tags)
+    x0 = out["pos"][:, :3] + out["image"][:, :3] * L
+    x1 = g["pos"][:, :3] + g["image"][:, :3] * L
+    assert np.max(np.abs(x1 - x0)) < 1e-9
+    assert np.max(np.abs(g["vel"][:, :3] - out["vel"][:, :3])) < 1e-8
+    assert np.allclose(th, out["thermo"], rtol=1e-9, atol=1e-9)
+    assert s.get_step() == 100
+
+
+def test_thermo_matches_oracle_and_is_reproducible():
+    st = equilibrated_lj()
+    L = st.box[0]
+    ref, vref, absf = oracle.lj_forces(st.pos, L, 2.5)
+    th_ref = oracle.thermo(st.vel, ref, vref, L)
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005)
+    s.prepare()
+    s.compute_pair(want_virial=True)
+    a = s.thermo().cpu().numpy()[0]
+    b = s.thermo().cpu().numpy()[0]
+    assert np.array_equal(a, b)
+    for k, name in enumerate(oracle.THERMO_FIELDS):
+        assert a[k] == pytest.approx(th_ref[name], rel=1e-11, abs=1e-9), name
+
+
+def test_sort_matches_oracle_order_and_keeps_forces():
+    st = lj_state(n=4000, jitter=0.3)
+    rng = np.random.default_rng(1)
+    perm = rng.permutation(st.n)  # scramble the input order
+    for k in ("pos", "vel", "image"):
+        setattr(st, k, getattr(st, k)[perm])
+    L = st.box[0]
+    order = oracle.sfc_order(st.pos, L, 2.8)
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005)
+    s.build_cells()
+    s.sort()
+    s.prepare()
+    g = s.state_numpy()
+    assert np.array_equal(g["tag"], order)  # tags were 0..N-1 in input order
+    assert np.array_equal(g["pos"], st.pos[order])
+    f = s.forces().cpu().numpy()
+    ref, _, absf = oracle.lj_forces(st.pos, L, 2.5)
+    fp64_force_check(f, ref[order], absf[order])
+
+
+def test_dpd_forces_invariant_under_sort():
+    st = inputs.dpd_fluid(3000, 3.0, 1.0, seed=32)
+    kw = dict(r_cut=1.0, r_skin=0.3, dt=0.02, pair="dpd", coeff=[[25.0, 4.5]], kT=1.0,
+              seed=5)
+    a = md.MDSystem(st, **kw)
+    a.prepare()
+    fa = a.forces().cpu().numpy()
+    b = md.MDSystem(st, **kw)
+    b.build_cells()
+    b.sort()
+    b.prepare()
+    fb = b.forces().cpu().numpy()
+    tag = b.tag.cpu().numpy()
+    assert not np.array_equal(tag, np.arange(st.n))
+    ref, _, absf = oracle.dpd_forces(st.pos, st.vel, st.box[0], 1.0, [[25.0, 4.5]], 1.0, 0.02,
+                                     0, 5)
+    fp64_force_check(fb, fa[tag], absf[tag])
+
+
+def test_rebuild_flag_follows_half_skin_rule():
+    st = lj_state(n=2048, jitter=0.05)
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.4, dt=0.005)
+    s.prepare()
+    b0 = s.info()["n_builds"]
+
+    def step_and_check_rebuild():
+        s.integrate(1)
+        s.build_cells(force=False)
+        s.build_nlist(force=False)
+        return s.info()["n_builds"] - b0
+
+    # zero velocities: particles move only by dt^2/2 F (< 1e-3), no rebuild
+    s.vel.zero_()
+    assert step_and_check_rebuild() == 0
+    # one particle moved by 0.21 > skin / 2 through its velocity: rebuild
+    s.vel.zero_()
+    s.vel[17, 0] = 0.21 / 0.005
+    assert step_and_check_rebuild() == 1
+    # the rebuilt list is exact for the positions it was built from
+    counts, rows = (x.cpu().numpy() for x in s.nlist())
+    cb, rb = oracle.neighbors(s.pos.cpu().numpy(), st.box[0], 2.9, max_nb=s.max_nb)
+    assert np.array_equal(counts, cb)
+    for i in range(st.n):
+        assert np.array_equal(np.sort(rows[i, :counts[i]]), rb[i, :cb[i]])
+    # 0.19 < skin / 2 since that build: no rebuild
+    s.vel.zero_()
+    s.vel[17, 0] = 0.19 / 0.005
+    assert step_and_check_rebuild() == 1
+
+
+def test_nlist_overflow_is_reported():
+    st = lj_state(n=2048)
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, max_nb=32)
+    s.build_cells()
+    s.build_nlist()
+    code, detail = s.poll_error()
+    assert code == 4 and detail > 32
+
+
+@pytest.mark.parametrize("prec", ("fp64", "mixed"))
+def test_nve_energy_drift(prec):
+    """Shifted-energy drift over 1e4 steps at dt = 0.005 after 1000
+    equilibration steps (N = 4000 fcc start, T = 1.44).  A single trajectory's
+    least-squares slope is dominated by slow energy fluctuations (the oracle's
+    own runs give 2.5e-5 .. 8.6e-5 for seeds 14..17), so the bound applies to
+    the mean over four seeded realizations; each one stays below 2e-4."""
+    drifts = []
+    for seed in (14, 15, 16, 17):
+        st = inputs.lj_fluid(4000, 0.8442, 1.44, seed=seed)
+        s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, precision=prec,
+                        shift_energy=True, thermo_period=10, graph_steps=100, sort_period=200)
+        s.run(1000)  # equilibrate from the lattice
+        th = s.run_with_thermo(10000).cpu().numpy()[:, 0, :]
+        s.check_error()
+        e = (th[:, 0] + th[:, 1]) / 4000
+        t = np.arange(e.size) * 10 * 0.005
+        drifts.append(abs(np.polyfit(t, e, 1)[0]) * 1e4 * 0.005)
+        assert np.max(np.abs(e - e[0])) < 1e-3
+        p_tot = np.abs(th[:, 5:8]).max()
+        assert p_tot < (1e-8 if prec == "fp64" else 1.0), p_tot
+        s.close()
+    assert np.mean(drifts) < 1e-4, drifts
+    assert max(drifts) < 2e-4, drifts
+
+
+def test_batched_replicas_equal_standalone_runs():
+    ens = inputs.replica_ensemble(6, seed=3, n_min=2000, n_max=6000, jitter=0.1)
+    kw = dict(r_cut=2.5, r_skin=0.3, dt=0.005)
+    b = md.MDSystem(ens, **kw)
+    b.prepare()
+    fb = b.forces().cpu().numpy()
+    for r in range(ens.n_replicas):
+        sub = inputs.select_replica(ens, r)
+        a = md.MDSystem(sub, **kw)
+        a.prepare()
+        fa = a.forces().cpu().numpy()
+        o0, o1 = ens.offsets[r], ens.offsets[r + 1]
+        assert np.array_equal(fa, fb[o0:o1]), r
+        ref, _, absf = oracle.lj_forces(sub.pos, sub.box[0], 2.5)
+        fp64_force_check(fa, ref, absf)
+    # and they stay equal over a run with rebuilds
+    b.run(60)
+    gb = b.state_numpy()
+    for r in (0, ens.n_replicas - 1):
+        sub = inputs.select_replica(ens, r)
+        a = md.MDSystem(sub, **kw)
+        a.run(60)
+        ga = a.state_numpy()
+        o0, o1 = ens.offsets[r], ens.offsets[r + 1]
+        assert np.array_equal(ga["pos"], gb["pos"][o0:o1])
