@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default="", help="fixed launch config, e.g. nlist:640:1,pair:128:1")
     return ap.parse_args()
 
 
@@ -248,9 +249,14 @@ def main():
     with torch.cuda.stream(stream):
         sysm = md.MDSystem(st, precision="mixed", stream=stream, **common)
         sysm.prepare(stream)
-        tuning = None
-        if not args.no_autotune:
-            tuning = sysm.autotune(n_samples=5, block_stride=2, stream=stream)
+        if args.tuning:
+            for item in args.tuning.split(","):
+                name, b, w = item.split(":")
+                sysm.set_tuning(md.KERNEL_NLIST if name == "nlist" else md.KERNEL_PAIR,
+                                int(b), int(w))
+            sysm.prepare(stream)
+        elif not args.no_autotune:
+            sysm.autotune(n_samples=5, block_stride=2, stream=stream)
         sysm.run(args.equil, stream=stream)  # melt the lattice start
         sysm.run(args.warmup, stream=stream)
         torch.cuda.synchronize()
@@ -339,8 +345,11 @@ def main():
             for k in ("pos", "vel", "image", "tag", "type"):
                 setattr(st64, k, eq_state[k])
             s64 = md.MDSystem(st64, precision="fp64", stream=stream, max_nb=max_nb, **common)
-            s64.set_tuning(md.KERNEL_PAIR, *tune_used["pair"])
-            s64.set_tuning(md.KERNEL_NLIST, *tune_used["nlist"])
+            for kern, name in ((md.KERNEL_PAIR, "pair"), (md.KERNEL_NLIST, "nlist")):
+                try:
+                    s64.set_tuning(kern, *tune_used[name])
+                except md.MDError:
+                    pass  # the FP64 kernel may not fit the mixed kernel's block size
             s64.run(3, stream=stream)
             t64 = time_steps(s64, args.fp64_steps, stream, torch)
             s64.check_error()
