@@ -231,6 +231,32 @@ md_status md_get_info(md_system *s, int64_t *n_cells, int32_t *max_nb,
 md_status md_philox4x32_10(const uint32_t *dev_in, uint32_t *dev_out, int64_t n,
                            md_stream stream);
 
+/* --- allocation-free entry point ----------------------------------------- */
+
+/* The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory at all (a plugin whose host program owns every
+ * device allocation, a real-time loop that cannot afford cudaMalloc's implicit
+ * synchronisation): it computes FP64 LJ 12-6 forces of ONE periodic system
+ * without a workspace, binning the particles into cells of width >= r_cut and
+ * summing every pair within r_cut over the 27 surrounding cells.
+ *   dev_pos    DEVICE double [n][4] (x, y, z in [0, box), w ignored), 16-B aligned
+ *   box        HOST double [3] edge lengths
+ *   dev_force  DEVICE double [n][4] output: F, per-particle energy (half of each
+ *              pair's unshifted V)
+ * Scratch: a 4 MiB array in the library's device memory (1,048,576 int32),
+ * reserved on every device the library is used on, until the process exits.
+ * A call needs 3 n + 2 n_cells of them, n_cells = product over the edges of
+ * min(floor(box / r_cut), 1024); larger systems get MD_ERR_WORKSPACE_TOO_SMALL
+ * before any launch.  Boxes under 3 cells per edge: MD_ERR_CELL_GRID.
+ * The first call on a device looks up the array's device address (with that
+ * device current): make that first call before any stream capture.  Calls use
+ * no cudaMalloc / cudaFree.  All calls share the one array, so calls that may
+ * overlap on the GPU (different streams, or different host threads) race:
+ * serialise them.  Enqueues on `stream` and returns without synchronising. */
+md_status md_lj_forces_noalloc(const double *dev_pos, int64_t n, const double *box,
+                               double r_cut, double epsilon, double sigma,
+                               double *dev_force, md_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

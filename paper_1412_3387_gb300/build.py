@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmdgb.so")
-SOURCES = ["api.cu", "k_cells.cu", "k_nlist.cu", "k_pair.cu", "k_integrate.cu"]
+SOURCES = ["api.cu", "k_cells.cu", "k_nlist.cu", "k_pair.cu", "k_integrate.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

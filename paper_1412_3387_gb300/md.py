@@ -74,6 +74,7 @@ SIGNATURES = {
     "md_get_cells": (C.c_int, [_P, _P, _P, _P, _P]),
     "md_get_info": (C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I64)]),
     "md_philox4x32_10": (C.c_int, [_P, _P, _I64, _P]),
+    "md_lj_forces_noalloc": (C.c_int, [_P, _I64, _P, _D, _D, _D, _P, _P]),
 }
 
 _lib = None
@@ -348,6 +349,22 @@ def philox4x32_10(inp, stream=None):
     check(lib.md_philox4x32_10(_ptr(dev_in), _ptr(dev_out), a.shape[0], _stream(stream)),
           "md_philox4x32_10")
     return dev_out.cpu().numpy().view(np.uint32)
+
+
+def lj_forces_noalloc(pos, box, r_cut, epsilon=1.0, sigma=1.0, stream=None):
+    """FP64 LJ forces of one system through md_lj_forces_noalloc, the entry
+    point for callers that cannot allocate device memory (it uses a fixed
+    4 MiB scratch array inside the library).  pos: float64 CUDA tensor [n, 4];
+    returns a float64 CUDA tensor [n, 4] (F, per-particle energy)."""
+    import torch
+    lib = load()
+    n = int(pos.shape[0])
+    out = torch.empty((n, 4), dtype=torch.float64, device=pos.device)
+    b = np.ascontiguousarray(np.broadcast_to(np.asarray(box, np.float64).reshape(-1), (3,)))
+    check(lib.md_lj_forces_noalloc(_ptr(pos), n, b.ctypes.data_as(C.c_void_p), float(r_cut),
+                                   float(epsilon), float(sigma), _ptr(out), _stream(stream)),
+          "md_lj_forces_noalloc")
+    return out
 
 
 def default_max_nb(state, r_list: float) -> int:
