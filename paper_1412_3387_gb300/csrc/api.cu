@@ -84,7 +84,7 @@ struct Plan {
   int64_t n = 0, n_pad = 0, n_cells = 0, n_chunks = 0, n_tchunks = 0;
   int32_t max_nb = 0;
   // byte offsets into the workspace
-  size_t o_rep, o_off, o_chunk_rep, o_tchunk_rep, o_cell_rank, o_cell_count, o_cell_start,
+  size_t o_rep, o_off, o_chunk_rep, o_tchunk_rep, o_cell_rank, o_stencil, o_cell_count, o_cell_start,
       o_chunk_sum, o_cell_idx, o_pcell, o_pslot, o_n_nb, o_rtag, o_pos4f, o_oref, o_vel4f, o_nl,
       o_force, o_virial, o_tpart, o_ds, o_rebuild, o_sort_now, o_last_sort, o_coeff, o_btab,
       o_s_pos, o_s_vel, o_s_img, o_s_tag, o_s_type, o_s_pos4f, o_s_oref, o_s_vel4f;
@@ -142,6 +142,7 @@ md_status make_plan(const md_params *p, Plan &pl) {
       rp.L[d] = L;
       rp.inv_L[d] = 1.0 / L;
       rp.h[d] = L / (double)rp.nc[d];
+      rp.half_h[d] = 0.5 * rp.h[d];
       rp.inv_h[d] = (double)rp.nc[d] / L;
       rp.hf[d] = (float)rp.h[d];
       hmax = std::max(hmax, rp.h[d]);
@@ -175,6 +176,7 @@ md_status make_plan(const md_params *p, Plan &pl) {
   pl.o_chunk_rep = take(sizeof(int32_t) * pl.n_chunks);
   pl.o_tchunk_rep = take(sizeof(int32_t) * pl.n_tchunks);
   pl.o_cell_rank = take(sizeof(int32_t) * pl.n_cells);
+  pl.o_stencil = take(sizeof(uint32_t) * 27 * (size_t)pl.n_cells);
   pl.o_cell_count = take(sizeof(int32_t) * pl.n_cells);
   pl.o_cell_start = take(sizeof(int32_t) * pl.n_cells);
   pl.o_chunk_sum = take(sizeof(int32_t) * pl.n_chunks);
@@ -327,6 +329,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   a.oref = at<float4>(ws, pl.o_oref);
   a.vel4f = dpd ? at<float4>(ws, pl.o_vel4f) : nullptr;
   a.cell_rank = at<int32_t>(ws, pl.o_cell_rank);
+  a.stencil = at<uint32_t>(ws, pl.o_stencil);
   a.cell_count = at<int32_t>(ws, pl.o_cell_count);
   a.cell_start = at<int32_t>(ws, pl.o_cell_start);
   a.chunk_sum = at<int32_t>(ws, pl.o_chunk_sum);
@@ -367,6 +370,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   a.dt = p->dt;
   a.mass = p->mass;
   a.kT = p->kT;
+  a.half_dt_m = 0.5 * p->dt / p->mass;
   a.seed = p->seed;
   a.disp2_f = (float)(0.25 * p->r_skin * p->r_skin * (1.0 - 1e-4));
   a.n_chunks = pl.n_chunks;
@@ -376,6 +380,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   // host tables
   std::vector<int32_t> chunk_rep(pl.n_chunks), tchunk_rep(pl.n_tchunks);
   std::vector<int32_t> rank(pl.n_cells, 0);
+  std::vector<uint32_t> stencil((size_t)pl.n_cells * 27, 0);
   for (int r = 0; r < R; r++) {
     const Rep &rp = pl.reps[r];
     for (int c = 0; c < rp.nchunk; c++) chunk_rep[rp.chunk0 + c] = r;
@@ -392,6 +397,22 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
         }
     std::sort(keys.begin(), keys.end());
     for (int32_t k = 0; k < rp.ncell; k++) rank[rp.cell0 + keys[k].second] = k;
+    // for every cell (by rank): its 27 neighbours (periodic), ascending rank,
+    // each tagged with the code (dx+1) + 3 (dy+1) + 9 (dz+1) of its offset
+    for (int32_t k = 0; k < rp.ncell; k++) {
+      const int32_t lin = keys[k].second;
+      const int x = lin % rp.nc[0], y = (lin / rp.nc[0]) % rp.nc[1], z = lin / (rp.nc[0] * rp.nc[1]);
+      uint32_t nb[27];
+      for (int code = 0; code < 27; code++) {
+        const int nx = (x + code % 3 - 1 + rp.nc[0]) % rp.nc[0];
+        const int ny = (y + (code / 3) % 3 - 1 + rp.nc[1]) % rp.nc[1];
+        const int nz = (z + code / 9 - 1 + rp.nc[2]) % rp.nc[2];
+        const int32_t nlin = nx + rp.nc[0] * (ny + rp.nc[1] * nz);
+        nb[code] = (uint32_t)rank[rp.cell0 + nlin] | ((uint32_t)code << kIdxBits);
+      }
+      std::sort(nb, nb + 27, [](uint32_t u, uint32_t v) { return (u & kIdxMask) < (v & kIdxMask); });
+      std::copy(nb, nb + 27, stencil.begin() + (size_t)(rp.cell0 + k) * 27);
+    }
   }
   std::vector<unsigned char> coeff(64 * (size_t)p->n_types * p->n_types, 0);
   for (int ti = 0; ti < p->n_types; ti++)
@@ -430,6 +451,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
       cudaMemcpyAsync(at<void>(ws, pl.o_chunk_rep), chunk_rep.data(), sizeof(int32_t) * pl.n_chunks, cudaMemcpyHostToDevice, stream) ||
       cudaMemcpyAsync(at<void>(ws, pl.o_tchunk_rep), tchunk_rep.data(), sizeof(int32_t) * pl.n_tchunks, cudaMemcpyHostToDevice, stream) ||
       cudaMemcpyAsync(at<void>(ws, pl.o_cell_rank), rank.data(), sizeof(int32_t) * pl.n_cells, cudaMemcpyHostToDevice, stream) ||
+      cudaMemcpyAsync(at<void>(ws, pl.o_stencil), stencil.data(), sizeof(uint32_t) * stencil.size(), cudaMemcpyHostToDevice, stream) ||
       cudaMemcpyAsync(at<void>(ws, pl.o_coeff), coeff.data(), coeff.size(), cudaMemcpyHostToDevice, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_cell_count), 0, sizeof(int32_t) * pl.n_cells, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_cell_start), 0, sizeof(int32_t) * pl.n_cells, stream) ||

@@ -142,9 +142,9 @@ __global__ void k_bin_scatter(KArgs a, int force) {
   int cy = cell_coord(x.y, rp.inv_h[1], rp.nc[1]);
   int cz = cell_coord(x.z, rp.inv_h[2], rp.nc[2]);
   float4 o;
-  o.x = frame_offset(x.x, cx, rp.h[0], rp.L[0]);
-  o.y = frame_offset(x.y, cy, rp.h[1], rp.L[1]);
-  o.z = frame_offset(x.z, cz, rp.h[2], rp.L[2]);
+  o.x = frame_offset_fast(x.x, cx, rp.h[0], rp.half_h[0], rp.L[0]);
+  o.y = frame_offset_fast(x.y, cy, rp.h[1], rp.half_h[1], rp.L[1]);
+  o.z = frame_offset_fast(x.z, cz, rp.h[2], rp.half_h[2], rp.L[2]);
   o.w = __uint_as_float(pack_cell(cx, cy, cz, a.type[i]));
   a.pos4f[i] = o;
   a.oref[i] = o;

@@ -35,11 +35,23 @@ __device__ __forceinline__ void st_d4(double4 *p, const double4 &v) {
 // step, where this equals the oracle's single subtraction); the fix-ups
 // absorb rounding at the box edge.  Non-finite x is left alone (and flagged
 // by the caller), so no loop depends on the value of x.
+// On GB300 FP64 instructions are scarce (a few per clock per SM), so the box
+// test uses the IEEE bit patterns: for x >= 0 and L > 0 the ordering of the
+// doubles is the ordering of their bits as signed 64-bit integers, and x < 0
+// (or -0) is the sign bit.  Finite <=> exponent bits not all ones.
+__device__ __forceinline__ bool outside_box(double x, long long Lbits) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 || b >= Lbits;
+}
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
 __device__ __forceinline__ void kick_drift(double &x, double &v, int &img, double f, double hk,
                                            double dt, double L) {
   v = __dadd_rn(v, __dmul_rn(hk, f));
   x = __dadd_rn(x, __dmul_rn(dt, v));
-  if ((x >= L || x < 0.0) && isfinite(x)) {
+  if (outside_box(x, __double_as_longlong(L)) && finite_bits(x)) {
     double k = floor(x / L);
     k = fmin(fmax(k, -1e9), 1e9);
     x = __dsub_rn(x, __dmul_rn(k, L));
@@ -66,7 +78,7 @@ __global__ void k_integrate1(KArgs a) {
     const double4 f = ld_force(a, i);
     int4 img = a.image[i];
     const int4 img0 = img;
-    const double hk = 0.5 * a.dt / a.mass;
+    const double hk = a.half_dt_m;
     kick_drift(x.x, v.x, img.x, f.x, hk, a.dt, rp.L[0]);
     kick_drift(x.y, v.y, img.y, f.y, hk, a.dt, rp.L[1]);
     kick_drift(x.z, v.z, img.z, f.z, hk, a.dt, rp.L[2]);
@@ -75,22 +87,26 @@ __global__ void k_integrate1(KArgs a) {
     if (img.x != img0.x || img.y != img0.y || img.z != img0.z) a.image[i] = img;
     float4 o = a.pos4f[i];
     const uint32_t w = __float_as_uint(o.w);
-    o.x = frame_offset(x.x, cell_x(w), rp.h[0], rp.L[0]);
-    o.y = frame_offset(x.y, cell_y(w), rp.h[1], rp.L[1]);
-    o.z = frame_offset(x.z, cell_z(w), rp.h[2], rp.L[2]);
+    o.x = frame_offset_fast(x.x, cell_x(w), rp.h[0], rp.half_h[0], rp.L[0]);
+    o.y = frame_offset_fast(x.y, cell_y(w), rp.h[1], rp.half_h[1], rp.L[1]);
+    o.z = frame_offset_fast(x.z, cell_z(w), rp.h[2], rp.half_h[2], rp.L[2]);
     a.pos4f[i] = o;
     const float4 ref = a.oref[i];
     const float ex = o.x - ref.x, ey = o.y - ref.y, ez = o.z - ref.z;
     const float d2 = ex * ex + ey * ey + ez * ez;
     if (!(d2 <= a.disp2_f)) a.rebuild[2 * r + par] = 1;  // NaN also triggers
-    if (!isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z)) {
+    if (!finite_bits(x.x) || !finite_bits(x.y) || !finite_bits(x.z)) {
       if (atomicOr(&a.ds->error, kErrNonfinite) == 0u) a.ds->error_detail = i;
     }
     if (a.vel4f) a.vel4f[i] = make_float4((float)v.x, (float)v.y, (float)v.z, __int_as_float(a.tag[i]));
   }
-  __threadfence();
+  // Block barrier, then one fence + ticket per block (release of every
+  // thread's flag store through the barrier).
   __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(&a.ds->blocks_done, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(&a.ds->blocks_done, 1u) == gridDim.x - 1;
+  }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
@@ -117,7 +133,7 @@ __global__ void k_integrate2(KArgs a) {
   if (i >= a.n) return;
   double4 v = ld_d4_plain(a.vel + i);
   const double4 f = ld_force(a, i);
-  const double hk = 0.5 * a.dt / a.mass;
+  const double hk = a.half_dt_m;
   v.x = __dadd_rn(v.x, __dmul_rn(hk, f.x));
   v.y = __dadd_rn(v.y, __dmul_rn(hk, f.y));
   v.z = __dadd_rn(v.z, __dmul_rn(hk, f.z));
@@ -264,9 +280,9 @@ __global__ void k_init_frames(KArgs a) {
   const int cy = cell_coord(x.y, rp.inv_h[1], rp.nc[1]);
   const int cz = cell_coord(x.z, rp.inv_h[2], rp.nc[2]);
   float4 o;
-  o.x = frame_offset(x.x, cx, rp.h[0], rp.L[0]);
-  o.y = frame_offset(x.y, cy, rp.h[1], rp.L[1]);
-  o.z = frame_offset(x.z, cz, rp.h[2], rp.L[2]);
+  o.x = frame_offset_fast(x.x, cx, rp.h[0], rp.half_h[0], rp.L[0]);
+  o.y = frame_offset_fast(x.y, cy, rp.h[1], rp.half_h[1], rp.L[1]);
+  o.z = frame_offset_fast(x.z, cz, rp.h[2], rp.half_h[2], rp.L[2]);
   // tags must be a permutation of 0..N-1 and types lie in [0, ntypes): both
   // index tables later, so out-of-range values are refused here
   const int32_t tg = a.tag[i], ty = a.type[i];

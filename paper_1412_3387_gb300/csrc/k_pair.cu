@@ -9,8 +9,10 @@
 //   FP64  -- FP64 distance (fixed-order minimum image) and FP64 force math.
 //   mixed -- separations from FP32 frame-relative offsets plus the FP32 shift
 //            of the neighbouring cell named by the entry's code; FP32 force
-//            math; per-lane Kahan-compensated FP32 sums merged across the W
-//            lanes with error-free two-sums.
+//            math; each lane sums the forces of a group of U entries plainly
+//            and adds the group sum to Kahan-compensated FP32 per-particle
+//            sums, which are merged across the W lanes with error-free
+//            two-sums.
 // In both forms the cut-off decision r^2 < r_cut^2 is the FP64 one: an FP32
 // r^2 inside a proven error band around r_cut^2 is re-tested in FP64.
 #include <algorithm>
@@ -60,7 +62,7 @@ __device__ __forceinline__ double seg_sum(double v) {
   return v;
 }
 
-template <int POT, int W, bool MIXED, bool ENERGY>
+template <int POT, int W, bool MIXED, bool ENERGY, bool ONE>
 __global__ void k_pair(KArgs a) {
   extern __shared__ float4 sh_shift[];  // [replicas spanned][27]
   constexpr unsigned FULL = 0xffffffffu;
@@ -103,92 +105,143 @@ __global__ void k_pair(KArgs a) {
     else { vi = ld_d4(a.vel + i); tag_i = a.tag[i]; }
   }
 
+  // single-type systems (ONE) keep the pair coefficients in registers
+  constexpr bool one_type = ONE;
+  LJCoeffF ljf0{};
+  LJCoeffD ljd0{};
+  DPDCoeffF dpf0{};
+  DPDCoeffD dpd0{};
+  if (one_type) {
+    if (POT == kLJ) {
+      if (MIXED) ljf0 = reinterpret_cast<const LJCoeffF *>(a.coeff)[0];
+      else ljd0 = reinterpret_cast<const LJCoeffD *>(a.coeff)[0];
+    } else {
+      if (MIXED) dpf0 = reinterpret_cast<const DPDCoeffF *>(a.coeff)[0];
+      else dpd0 = reinterpret_cast<const DPDCoeffD *>(a.coeff)[0];
+    }
+  }
+
   // accumulators
   KSum kf[3], kpe, kw[6];
   double df[3] = {0., 0., 0.}, dpe = 0., dw[6] = {0., 0., 0., 0., 0., 0.};
 
-  const int iters = __reduce_max_sync(FULL, (unsigned)((nn + W - 1) / W));
+  // Lane sl handles entries k = t W + sl, t < mine.  Entries are fetched U at a
+  // time, one group ahead of use (double buffer in registers), and the U
+  // position gathers of a group are independent, so each lane keeps several
+  // list loads and gathers in flight.
+  constexpr int U = 4;
+  constexpr uint32_t kNone = 0xffffffffu;  // code 31: no entry
+  const int mine = nn > sl ? (nn - sl + W - 1) / W : 0;
+  const int iters = __reduce_max_sync(FULL, (unsigned)mine);
   const uint32_t *row = a.nl + (((size_t)i) << LW) + sl;
   const size_t pitch = ((size_t)a.n_pad) << LW;
-  for (int t = 0; t < iters; t++) {
-    const int k = t * W + sl;
-    if (k >= nn) continue;
-    const uint32_t e = __ldcs(row + (size_t)t * pitch);
-    const int32_t j = (int32_t)(e & kIdxMask);
-    const float4 oj = __ldg(a.pos4f + j);
-    const float4 sh = shift[e >> kIdxBits];
-    const float dx = (oi.x - oj.x) - sh.x;
-    const float dy = (oi.y - oj.y) - sh.y;
-    const float dz = (oi.z - oj.z) - sh.z;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-    if (r2 >= rc2_hi) continue;
-    const int tj = cell_type(__float_as_uint(oj.w));
-    const int cidx = ti * a.ntypes + tj;
-    if (MIXED) {
-      if (r2 > rc2_lo) {
+  uint32_t ebuf[U];
+  const uint32_t *rp_next = row;
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    ebuf[u] = u < mine ? __ldcs(rp_next) : kNone;
+    rp_next += pitch;
+  }
+  for (int t0 = 0; t0 < iters; t0 += U) {
+    uint32_t ecur[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      ecur[u] = ebuf[u];
+      ebuf[u] = t0 + U + u < mine ? __ldcs(rp_next) : kNone;
+      rp_next += pitch;
+    }
+    // forces of this group are summed plainly, then added to the running
+    // Kahan-compensated per-particle sums (one compensated add per group)
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    float4 ojs[U];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      ojs[u] = ecur[u] != kNone ? __ldg(a.pos4f + (ecur[u] & kIdxMask)) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const uint32_t e = ecur[u];
+      if (e == kNone) continue;
+      const int32_t j = (int32_t)(e & kIdxMask);
+      const float4 oj = ojs[u];
+      const float4 sh = shift[e >> kIdxBits];
+      const float dx = (oi.x - oj.x) - sh.x;
+      const float dy = (oi.y - oj.y) - sh.y;
+      const float dz = (oi.z - oj.z) - sh.z;
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      if (r2 >= rc2_hi) continue;
+      const int tj = cell_type(__float_as_uint(oj.w));
+      const int cidx = ti * a.ntypes + tj;
+      if (MIXED) {
+        if (r2 > rc2_lo) {
+          double d[3];
+          if (exact_r2(ld_d4(a.pos + i), ld_d4(a.pos + j), rp, d) >= a.rc2) continue;
+        }
+        float fr, v = 0.f;
+        if (POT == kLJ) {
+          const LJCoeffF c = one_type ? ljf0 : reinterpret_cast<const LJCoeffF *>(a.coeff)[cidx];
+          const float r2i = __fdividef(1.0f, r2);
+          const float r6 = r2i * r2i * r2i;
+          fr = r2i * r6 * (c.lj1 * r6 - c.lj2);
+          if (ENERGY) v = r6 * (c.lj3 * r6 - c.lj4) - c.vshift;
+        } else {
+          const DPDCoeffF c = one_type ? dpf0 : reinterpret_cast<const DPDCoeffF *>(a.coeff)[cidx];
+          const float4 vj = __ldg(a.vel4f + j);
+          const float rinv = rsqrtf(r2);
+          const float rr = r2 * rinv;
+          const float w = 1.f - rr * inv_rc;
+          const float dot = dx * (vi4.x - vj.x) + dy * (vi4.y - vj.y) + dz * (vi4.z - vj.z);
+          const uint32_t word = dpd_word(tag_i, __float_as_int(vj.w), (uint64_t)step, a.seed);
+          const float uu = ((float)(word >> 8) + 0.5f) * 5.9604644775390625e-08f;  // 2^-24
+          const float theta = 1.7320508075688772f * (2.f * uu - 1.f);
+          const float fmag = c.A * w - c.gamma * w * w * dot * rinv + c.sigma_rdt * w * theta;
+          fr = fmag * rinv;
+          if (ENERGY) v = 0.5f * c.A * (float)a.r_cut * w * w;
+        }
+        const float fx = fr * dx, fy = fr * dy, fz = fr * dz;
+        gx += fx; gy += fy; gz += fz;
+        if (ENERGY) {
+          kpe.add(0.5f * v);
+          kw[0].add(0.5f * dx * fx); kw[1].add(0.5f * dx * fy); kw[2].add(0.5f * dx * fz);
+          kw[3].add(0.5f * dy * fy); kw[4].add(0.5f * dy * fz); kw[5].add(0.5f * dz * fz);
+        }
+      } else {
         double d[3];
-        if (exact_r2(ld_d4(a.pos + i), ld_d4(a.pos + j), rp, d) >= a.rc2) continue;
+        const double r2d = exact_r2(pi, ld_d4(a.pos + j), rp, d);
+        if (r2d >= a.rc2) continue;
+        double fr, v = 0.;
+        if (POT == kLJ) {
+          const LJCoeffD c = one_type ? ljd0 : reinterpret_cast<const LJCoeffD *>(a.coeff)[cidx];
+          const double r2i = __drcp_rn(r2d);
+          const double r6 = r2i * r2i * r2i;
+          fr = r2i * r6 * (c.lj1 * r6 - c.lj2);
+          if (ENERGY) v = r6 * (c.lj3 * r6 - c.lj4) - c.vshift;
+        } else {
+          const DPDCoeffD c = one_type ? dpd0 : reinterpret_cast<const DPDCoeffD *>(a.coeff)[cidx];
+          const double4 vj = ld_d4(a.vel + j);
+          const double rr = sqrt(r2d);
+          const double rinv = 1.0 / rr;
+          const double w = 1.0 - rr / a.r_cut;
+          const double dot = d[0] * (vi.x - vj.x) + d[1] * (vi.y - vj.y) + d[2] * (vi.z - vj.z);
+          const uint32_t word = dpd_word(tag_i, a.tag[j], (uint64_t)step, a.seed);
+          const double uu = ((double)word + 0.5) * 2.3283064365386963e-10;  // 2^-32
+          const double theta = 1.7320508075688772 * (2.0 * uu - 1.0);
+          const double fmag = c.A * w - c.gamma * w * w * dot * rinv + c.sigma_rdt * w * theta;
+          fr = fmag * rinv;
+          if (ENERGY) v = 0.5 * c.A * a.r_cut * w * w;
+        }
+        const double fx = fr * d[0], fy = fr * d[1], fz = fr * d[2];
+        df[0] += fx; df[1] += fy; df[2] += fz;
+        if (ENERGY) {
+          dpe += 0.5 * v;
+          dw[0] += 0.5 * d[0] * fx; dw[1] += 0.5 * d[0] * fy; dw[2] += 0.5 * d[0] * fz;
+          dw[3] += 0.5 * d[1] * fy; dw[4] += 0.5 * d[1] * fz; dw[5] += 0.5 * d[2] * fz;
+        }
       }
-      float fr, v = 0.f;
-      if (POT == kLJ) {
-        const LJCoeffF c = reinterpret_cast<const LJCoeffF *>(a.coeff)[cidx];
-        const float r2i = __frcp_rn(r2);
-        const float r6 = r2i * r2i * r2i;
-        fr = r2i * r6 * (c.lj1 * r6 - c.lj2);
-        if (ENERGY) v = r6 * (c.lj3 * r6 - c.lj4) - c.vshift;
-      } else {
-        const DPDCoeffF c = reinterpret_cast<const DPDCoeffF *>(a.coeff)[cidx];
-        const float4 vj = __ldg(a.vel4f + j);
-        const float rinv = rsqrtf(r2);
-        const float rr = r2 * rinv;
-        const float w = 1.f - rr * inv_rc;
-        const float dot = dx * (vi4.x - vj.x) + dy * (vi4.y - vj.y) + dz * (vi4.z - vj.z);
-        const uint32_t word = dpd_word(tag_i, __float_as_int(vj.w), (uint64_t)step, a.seed);
-        const float u = ((float)(word >> 8) + 0.5f) * 5.9604644775390625e-08f;  // 2^-24
-        const float theta = 1.7320508075688772f * (2.f * u - 1.f);
-        const float fmag = c.A * w - c.gamma * w * w * dot * rinv + c.sigma_rdt * w * theta;
-        fr = fmag * rinv;
-        if (ENERGY) v = 0.5f * c.A * (float)a.r_cut * w * w;
-      }
-      const float fx = fr * dx, fy = fr * dy, fz = fr * dz;
-      kf[0].add(fx); kf[1].add(fy); kf[2].add(fz);
-      if (ENERGY) {
-        kpe.add(0.5f * v);
-        kw[0].add(0.5f * dx * fx); kw[1].add(0.5f * dx * fy); kw[2].add(0.5f * dx * fz);
-        kw[3].add(0.5f * dy * fy); kw[4].add(0.5f * dy * fz); kw[5].add(0.5f * dz * fz);
-      }
-    } else {
-      double d[3];
-      const double r2d = exact_r2(pi, ld_d4(a.pos + j), rp, d);
-      if (r2d >= a.rc2) continue;
-      double fr, v = 0.;
-      if (POT == kLJ) {
-        const LJCoeffD c = reinterpret_cast<const LJCoeffD *>(a.coeff)[cidx];
-        const double r2i = __drcp_rn(r2d);
-        const double r6 = r2i * r2i * r2i;
-        fr = r2i * r6 * (c.lj1 * r6 - c.lj2);
-        if (ENERGY) v = r6 * (c.lj3 * r6 - c.lj4) - c.vshift;
-      } else {
-        const DPDCoeffD c = reinterpret_cast<const DPDCoeffD *>(a.coeff)[cidx];
-        const double4 vj = ld_d4(a.vel + j);
-        const double rr = sqrt(r2d);
-        const double rinv = 1.0 / rr;
-        const double w = 1.0 - rr / a.r_cut;
-        const double dot = d[0] * (vi.x - vj.x) + d[1] * (vi.y - vj.y) + d[2] * (vi.z - vj.z);
-        const uint32_t word = dpd_word(tag_i, a.tag[j], (uint64_t)step, a.seed);
-        const double u = ((double)word + 0.5) * 2.3283064365386963e-10;  // 2^-32
-        const double theta = 1.7320508075688772 * (2.0 * u - 1.0);
-        const double fmag = c.A * w - c.gamma * w * w * dot * rinv + c.sigma_rdt * w * theta;
-        fr = fmag * rinv;
-        if (ENERGY) v = 0.5 * c.A * a.r_cut * w * w;
-      }
-      const double fx = fr * d[0], fy = fr * d[1], fz = fr * d[2];
-      df[0] += fx; df[1] += fy; df[2] += fz;
-      if (ENERGY) {
-        dpe += 0.5 * v;
-        dw[0] += 0.5 * d[0] * fx; dw[1] += 0.5 * d[0] * fy; dw[2] += 0.5 * d[0] * fz;
-        dw[3] += 0.5 * d[1] * fy; dw[4] += 0.5 * d[1] * fz; dw[5] += 0.5 * d[2] * fz;
-      }
+    }
+    if (MIXED) {
+      kf[0].add(gx);
+      kf[1].add(gy);
+      kf[2].add(gz);
     }
   }
 
@@ -236,7 +289,8 @@ cudaError_t go(const KArgs &a, int block, int span, cudaStream_t st) {
   int per_block = block / W;
   unsigned grid = (unsigned)((a.n + per_block - 1) / per_block);
   size_t smem = (size_t)span * 27 * sizeof(float4);
-  k_pair<POT, W, MIXED, ENERGY><<<grid, block, smem, st>>>(a);
+  if (a.ntypes == 1) k_pair<POT, W, MIXED, ENERGY, true><<<grid, block, smem, st>>>(a);
+  else k_pair<POT, W, MIXED, ENERGY, false><<<grid, block, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -253,19 +307,25 @@ cudaError_t go_w(const KArgs &a, Launch l, int span, cudaStream_t st) {
   }
 }
 
+template <int POT, int W, bool MIXED, bool ENERGY>
+int maxb_w() {
+  cudaFuncAttributes a1, a2;
+  if (cudaFuncGetAttributes(&a1, k_pair<POT, W, MIXED, ENERGY, true>) != cudaSuccess) return 0;
+  if (cudaFuncGetAttributes(&a2, k_pair<POT, W, MIXED, ENERGY, false>) != cudaSuccess) return 0;
+  return a1.maxThreadsPerBlock < a2.maxThreadsPerBlock ? a1.maxThreadsPerBlock : a2.maxThreadsPerBlock;
+}
+
 template <int POT, bool MIXED, bool ENERGY>
 int maxb(int w) {
-  cudaFuncAttributes at;
-  cudaError_t e = cudaErrorInvalidValue;
   switch (w) {
-    case 1: e = cudaFuncGetAttributes(&at, k_pair<POT, 1, MIXED, ENERGY>); break;
-    case 2: e = cudaFuncGetAttributes(&at, k_pair<POT, 2, MIXED, ENERGY>); break;
-    case 4: e = cudaFuncGetAttributes(&at, k_pair<POT, 4, MIXED, ENERGY>); break;
-    case 8: e = cudaFuncGetAttributes(&at, k_pair<POT, 8, MIXED, ENERGY>); break;
-    case 16: e = cudaFuncGetAttributes(&at, k_pair<POT, 16, MIXED, ENERGY>); break;
-    case 32: e = cudaFuncGetAttributes(&at, k_pair<POT, 32, MIXED, ENERGY>); break;
+    case 1: return maxb_w<POT, 1, MIXED, ENERGY>();
+    case 2: return maxb_w<POT, 2, MIXED, ENERGY>();
+    case 4: return maxb_w<POT, 4, MIXED, ENERGY>();
+    case 8: return maxb_w<POT, 8, MIXED, ENERGY>();
+    case 16: return maxb_w<POT, 16, MIXED, ENERGY>();
+    case 32: return maxb_w<POT, 32, MIXED, ENERGY>();
   }
-  return e == cudaSuccess ? at.maxThreadsPerBlock : 0;
+  return 0;
 }
 
 }  // namespace

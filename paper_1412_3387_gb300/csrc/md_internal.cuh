@@ -41,6 +41,7 @@ struct Rep {
   double L[3];
   double inv_L[3];
   double h[3];        // L / nc
+  double half_h[3];   // h / 2
   double inv_h[3];    // nc / L
   float hf[3];        // float(h): shift of a neighbouring cell's frame
   float band;         // FP32 r^2 uncertainty band (see DESIGN: exact decisions)
@@ -89,6 +90,7 @@ struct KArgs {
   float4 *oref;        // frame-relative position at the last build
   float4 *vel4f;       // FP32 velocity, tag bits in w (DPD mixed)
   int32_t *cell_rank;  // [cells] linear cell -> Hilbert rank (per replica)
+  const uint32_t *stencil;  // [cells][27] neighbour cells by ascending rank | code << 27
   int32_t *cell_count; // [cells]
   int32_t *cell_start; // [cells] first particle (global index)
   int32_t *chunk_sum;  // [chunks]
@@ -122,6 +124,7 @@ struct KArgs {
   double r_cut, rc2, rl2;
   float rc2f, rl2f;
   double dt, mass, kT;
+  double half_dt_m;    // dt / (2 m), computed once on the host
   double bond_K, bond_r0;
   float disp2_f;       // (r_skin / 2)^2, slightly reduced
   uint64_t seed;
@@ -156,11 +159,16 @@ __device__ __forceinline__ int cell_coord(double x, double inv_h, int nc) {
   return c < 0 ? 0 : c;
 }
 
-// FP32 offset of x from the centre of frame cell c, folded into (-L/2, L/2].
-__device__ __forceinline__ float frame_offset(double x, int c, double h, double L) {
-  double d = x - ((double)c + 0.5) * h;
-  if (d > 0.5 * L) d -= L;
-  else if (d < -0.5 * L) d += L;
+// FP32 offset of x from the centre (c + 1/2) h of frame cell c, folded into
+// (-L/2, L/2].  FP64 instructions are scarce on GB300, so the centre is one
+// FP64 multiply-add and the periodic fold (needed only once the particle has
+// crossed the box since its frame was set) is decided on the FP32 value: the
+// offsets stay below h + skin << L/2, far from the fold's threshold.
+__device__ __forceinline__ float frame_offset_fast(double x, int c, double h, double half_h,
+                                                   double L) {
+  double d = x - fma((double)c, h, half_h);
+  const float df = (float)d;
+  if (fabsf(df) > 0.5f * (float)L) d += df > 0.f ? -L : L;
   return (float)d;
 }
 
