@@ -70,7 +70,7 @@ def workload_config(args):
             "n_particles": args.n, "density": HEADLINE["rho"], "T": HEADLINE["T"],
             "r_cut": HEADLINE["r_cut"], "r_skin": HEADLINE["r_skin"], "dt": HEADLINE["dt"],
             "precision": "mixed (FP32 forces, Kahan; FP64 positions)",
-            "graph_steps": 100, "thermo_period": 100, "sort_period": 100,
+            "graph_steps": 100, "thermo_period": 100, "sort_period": 1,
             "l2": "inputs larger than L2 (about 40 B/particle resident state x 16.7M)"}
 
 
@@ -247,8 +247,10 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     H = HEADLINE
     st = inputs.lj_fluid(args.n, H["rho"], H["T"], seed=12345 + rank)
+    # sort_period=1: particles are re-sorted along the space-filling curve at
+    # every list rebuild, which keeps the cell members contiguous in memory
     common = dict(r_cut=H["r_cut"], r_skin=H["r_skin"], dt=H["dt"], thermo_period=100,
-                  graph_steps=100, sort_period=100, device=dev)
+                  graph_steps=100, sort_period=1, device=dev)
     with torch.cuda.stream(stream):
         sysm = md.MDSystem(st, precision="mixed", stream=stream, **common)
         sysm.prepare(stream)
@@ -372,7 +374,7 @@ def main():
             # batched ensemble: 256 LJ replicas, N log-uniform in [2000, 64000]
             ens = inputs.replica_ensemble(256, seed=777 + rank)
             sb = md.MDSystem(ens, r_cut=2.5, r_skin=0.3, dt=0.005, precision="mixed",
-                             thermo_period=100, graph_steps=100, sort_period=100, device=dev,
+                             thermo_period=100, graph_steps=100, sort_period=1, device=dev,
                              stream=stream)
             sb.prepare(stream)
             sb.run(300, stream=stream)

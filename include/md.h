@@ -141,7 +141,9 @@ md_status md_sort_particles(md_system *s, int32_t force, md_stream stream);
 
 /* Cell-list binning (Sec. 4.3.3, Sec. 5.1): counts per cell, exclusive scan,
  * scatter, then particles ordered by index inside each cell.  force = 0: only
- * replicas whose rebuild flag was raised by md_integrate(half = 1). */
+ * replicas whose rebuild flag was raised by md_integrate(half = 1).  The
+ * neighbour list refers to the binning it was built from: after a forced
+ * binning, md_compute_pair returns MD_ERR_STATE until md_build_nlist ran. */
 md_status md_build_cells(md_system *s, int32_t force, md_stream stream);
 
 /* Neighbour list (Sec. 5.1, Fig. "nlist"): w threads per particle stride over

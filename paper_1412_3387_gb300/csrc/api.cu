@@ -13,9 +13,6 @@
 
 using namespace mdgb;
 
-namespace mdgb {
-cudaError_t launch_pair_span(const KArgs &a, Launch l, int want_virial, int span, cudaStream_t st);
-}
 
 struct md_system {
   md_params p{};
@@ -25,8 +22,7 @@ struct md_system {
   md_particles parts{};
   KArgs a{};
   std::vector<Rep> reps;
-  Launch tune[2]{{256, 8}, {256, 4}};  // nlist, pair
-  int span_pair = 1;
+  Launch tune[2]{{128, 1}, {128, 1}};  // nlist, pair
   bool built = false;   // list built and forces computed (ready to step)
   bool binned = false;  // cells binned at least once
   bool listed = false;  // list built in the current layout
@@ -83,10 +79,11 @@ struct Plan {
   std::vector<Rep> reps;
   int64_t n = 0, n_pad = 0, n_cells = 0, n_chunks = 0, n_tchunks = 0;
   int32_t max_nb = 0;
+  int32_t stage_cap = 0;
   // byte offsets into the workspace
   size_t o_rep, o_off, o_chunk_rep, o_tchunk_rep, o_cell_rank, o_stencil, o_cell_count, o_cell_start,
       o_chunk_sum, o_cell_idx, o_pcell, o_pslot, o_n_nb, o_rtag, o_pos4f, o_oref, o_vel4f, o_nl,
-      o_force, o_virial, o_tpart, o_ds, o_rebuild, o_sort_now, o_last_sort, o_coeff, o_btab,
+      o_force, o_virial, o_tpart, o_ds, o_rebuild, o_sort_now, o_last_sort, o_ident, o_coeff, o_btab,
       o_s_pos, o_s_vel, o_s_img, o_s_tag, o_s_type, o_s_pos4f, o_s_oref, o_s_vel4f;
   size_t total = 0;
 };
@@ -163,6 +160,13 @@ md_status make_plan(const md_params *p, Plan &pl) {
     chunk0 += rp.nchunk;
     tchunk0 += rp.ntchunk;
   }
+  // stage capacity per warp: 15 % above the mean stencil population of the
+  // densest replica (denser neighbourhoods are processed in windows)
+  double dens = 0.0;
+  for (const Rep &rp : pl.reps)
+    if (rp.ncell > 0) dens = std::max(dens, (double)(rp.p1 - rp.p0) / rp.ncell);
+  int cap = (int)std::ceil((1.15 * 27.0 * dens + 32.0) / 32.0) * 32;
+  pl.stage_cap = std::min(std::max(cap, 128), 27 * kMaxCellSort);
   pl.n_cells = cell0;
   pl.n_chunks = chunk0;
   pl.n_tchunks = tchunk0;
@@ -188,7 +192,7 @@ md_status make_plan(const md_params *p, Plan &pl) {
   pl.o_pos4f = take(sizeof(float4) * NP);
   pl.o_oref = take(sizeof(float4) * NP);
   pl.o_vel4f = dpd ? take(sizeof(float4) * NP) : 0;
-  pl.o_nl = take(sizeof(uint32_t) * (size_t)pl.max_nb * NP);
+  pl.o_nl = take(sizeof(uint16_t) * (size_t)pl.max_nb * NP);
   pl.o_force = take((mixed ? sizeof(float4) : sizeof(double4)) * NP);
   pl.o_virial = take((mixed ? sizeof(float) : sizeof(double)) * 6 * NP);
   pl.o_tpart = take(sizeof(double) * 8 * pl.n_tchunks);
@@ -196,6 +200,7 @@ md_status make_plan(const md_params *p, Plan &pl) {
   pl.o_rebuild = take(sizeof(int32_t) * 2 * R);
   pl.o_sort_now = take(sizeof(int32_t) * R);
   pl.o_last_sort = take(sizeof(int64_t) * R);
+  pl.o_ident = take(sizeof(int32_t) * R);
   pl.o_coeff = take(64 * (size_t)p->n_types * p->n_types);
   pl.o_btab = take(sizeof(int32_t) * (size_t)std::max(p->max_bonds, 0) * N);
   pl.o_s_pos = take(sizeof(double4) * N);
@@ -219,7 +224,7 @@ md_status enqueue_step(md_system *s, int want_virial, cudaStream_t st) {
   MD_CUDA(launch_bin(a, 0, st));
   if (s->p.sort_period > 0) MD_CUDA(launch_sort(a, 0, st));
   MD_CUDA(launch_nlist(a, s->tune[MD_KERNEL_NLIST], 0, st));
-  MD_CUDA(launch_pair_span(a, s->tune[MD_KERNEL_PAIR], want_virial, s->span_pair, st));
+  MD_CUDA(launch_pair(a, s->tune[MD_KERNEL_PAIR], want_virial, st));
   if (s->n_bonds > 0) MD_CUDA(launch_bonds(a, want_virial, st));
   MD_CUDA(launch_integrate2(a, st));
   return MD_OK;
@@ -231,7 +236,7 @@ md_status prepare(md_system *s, cudaStream_t st) {
   s->binned = true;
   MD_CUDA(launch_nlist(s->a, s->tune[MD_KERNEL_NLIST], 1, st));
   s->listed = true;
-  MD_CUDA(launch_pair_span(s->a, s->tune[MD_KERNEL_PAIR], 0, s->span_pair, st));
+  MD_CUDA(launch_pair(s->a, s->tune[MD_KERNEL_PAIR], 0, st));
   if (s->n_bonds > 0) MD_CUDA(launch_bonds(s->a, 0, st));
   s->built = true;
   return MD_OK;
@@ -240,7 +245,6 @@ md_status prepare(md_system *s, cudaStream_t st) {
 void set_pair_w(md_system *s, Launch l) {
   s->tune[MD_KERNEL_PAIR] = l;
   s->a.w_store_log2 = ilog2(l.w);
-  s->span_pair = pair_span(s->off.data(), s->p.n_replicas, s->a.n, l.block / l.w);
   s->gvalid = false;
 }
 
@@ -294,6 +298,12 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
     return MD_ERR_INVALID_ARG;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
 
+  static bool attributes_set = false;  // opt the kernels into large shared memory once
+  if (!attributes_set) {
+    nlist_init_attributes();
+    pair_init_attributes();
+    attributes_set = true;
+  }
   md_system *s = new (std::nothrow) md_system();
   if (!s) return MD_ERR_INVALID_ARG;
   s->p = *p;
@@ -336,7 +346,8 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   a.cell_idx = at<int32_t>(ws, pl.o_cell_idx);
   a.pcell = at<int32_t>(ws, pl.o_pcell);
   a.pslot = at<int32_t>(ws, pl.o_pslot);
-  a.nl = at<uint32_t>(ws, pl.o_nl);
+  a.nl = at<uint16_t>(ws, pl.o_nl);
+  a.stage_cap = pl.stage_cap;
   a.n_nb = at<int32_t>(ws, pl.o_n_nb);
   a.force = at<void>(ws, pl.o_force);
   a.virial = at<void>(ws, pl.o_virial);
@@ -345,6 +356,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   a.rebuild = at<int32_t>(ws, pl.o_rebuild);
   a.sort_now = at<int32_t>(ws, pl.o_sort_now);
   a.last_sort = at<int64_t>(ws, pl.o_last_sort);
+  a.ident = at<int32_t>(ws, pl.o_ident);
   a.rtag = at<int32_t>(ws, pl.o_rtag);
   a.btab = p->max_bonds > 0 ? at<int32_t>(ws, pl.o_btab) : nullptr;
   a.s_pos = at<double4>(ws, pl.o_s_pos);
@@ -456,7 +468,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
       cudaMemsetAsync(at<void>(ws, pl.o_cell_count), 0, sizeof(int32_t) * pl.n_cells, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_cell_start), 0, sizeof(int32_t) * pl.n_cells, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_n_nb), 0, sizeof(int32_t) * pl.n_pad, stream) ||
-      cudaMemsetAsync(at<void>(ws, pl.o_nl), 0, sizeof(uint32_t) * (size_t)pl.max_nb * pl.n_pad, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_nl), 0, sizeof(uint16_t) * (size_t)pl.max_nb * pl.n_pad, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_rtag), 0, sizeof(int32_t) * pl.n, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_pcell), 0, sizeof(int32_t) * pl.n, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_pslot), 0, sizeof(int32_t) * pl.n, stream) ||
@@ -465,7 +477,8 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
       cudaMemsetAsync(at<void>(ws, pl.o_ds), 0, sizeof(DevState), stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_rebuild), 0, sizeof(int32_t) * 2 * R, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_sort_now), 0, sizeof(int32_t) * R, stream) ||
-      cudaMemsetAsync(at<void>(ws, pl.o_last_sort), 0, sizeof(int64_t) * R, stream))
+      cudaMemsetAsync(at<void>(ws, pl.o_last_sort), 0, sizeof(int64_t) * R, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_ident), 0, sizeof(int32_t) * R, stream))
     return fail(MD_ERR_CUDA);
   if (p->max_bonds > 0 &&
       cudaMemsetAsync(at<void>(ws, pl.o_btab), 0xff, sizeof(int32_t) * (size_t)p->max_bonds * pl.n, stream))
@@ -530,7 +543,11 @@ md_status md_sort_particles(md_system *s, int32_t force, md_stream stream) {
 md_status md_build_cells(md_system *s, int32_t force, md_stream stream) {
   if (!s) return MD_ERR_INVALID_ARG;
   MD_CUDA(launch_bin(s->a, force ? 1 : 0, reinterpret_cast<cudaStream_t>(stream)));
-  if (force) s->binned = true;
+  if (force) {
+    s->binned = true;
+    s->listed = false;  // rows refer to the cell stages of the previous binning
+    s->built = false;
+  }
   return MD_OK;
 }
 
@@ -546,8 +563,8 @@ md_status md_build_nlist(md_system *s, int32_t force, md_stream stream) {
 md_status md_compute_pair(md_system *s, int32_t want_virial, md_stream stream) {
   if (!s) return MD_ERR_INVALID_ARG;
   if (!s->listed) return MD_ERR_STATE;  // no list in the current layout yet
-  MD_CUDA(launch_pair_span(s->a, s->tune[MD_KERNEL_PAIR], want_virial ? 1 : 0, s->span_pair,
-                           reinterpret_cast<cudaStream_t>(stream)));
+  MD_CUDA(launch_pair(s->a, s->tune[MD_KERNEL_PAIR], want_virial ? 1 : 0,
+                      reinterpret_cast<cudaStream_t>(stream)));
   return MD_OK;
 }
 
@@ -635,7 +652,7 @@ md_status md_set_tuning(md_system *s, int32_t kernel, int32_t block, int32_t w) 
   if (!s || (kernel != MD_KERNEL_NLIST && kernel != MD_KERNEL_PAIR) || !valid_launch(block, w))
     return MD_ERR_INVALID_ARG;
   const int mb = kernel == MD_KERNEL_NLIST
-                     ? max_block_nlist(w)
+                     ? max_block_nlist(w, s->a.stage_cap)
                      : std::min(max_block_pair(s->a, w, 0), max_block_pair(s->a, w, 1));
   if (block > mb) return MD_ERR_INVALID_ARG;
   if (kernel == MD_KERNEL_NLIST) {
@@ -691,7 +708,7 @@ md_status md_autotune(md_system *s, int32_t n_samples, int32_t block_stride, md_
     for (int b = 32 * block_stride; b <= std::min(1024, mb); b += 32 * block_stride) {
       if (b < w) continue;
       set_pair_w(s, Launch{b, w});
-      const float t = median_time([&] { return launch_pair_span(s->a, Launch{b, w}, 0, s->span_pair, st); });
+      const float t = median_time([&] { return launch_pair(s->a, Launch{b, w}, 0, st); });
       if (t < 0) { cudaGetLastError(); continue; }
       if (t < best_t) { best_t = t; best_pair = Launch{b, w}; }
     }
@@ -702,7 +719,7 @@ md_status md_autotune(md_system *s, int32_t n_samples, int32_t block_stride, md_
   best_t = 1e30f;
   for (int w : ws) {
     if (result != MD_OK) break;
-    const int mb = max_block_nlist(w);
+    const int mb = max_block_nlist(w, s->a.stage_cap);
     for (int b = 32 * block_stride; b <= std::min(1024, mb); b += 32 * block_stride) {
       if (b < w) continue;
       const float t = median_time([&] { return launch_nlist(s->a, Launch{b, w}, 1, st); });
@@ -712,7 +729,7 @@ md_status md_autotune(md_system *s, int32_t n_samples, int32_t block_stride, md_
   }
   s->tune[MD_KERNEL_NLIST] = best_nl;
   if (result == MD_OK && launch_nlist(s->a, best_nl, 1, st) != cudaSuccess) result = MD_ERR_CUDA;
-  if (result == MD_OK && launch_pair_span(s->a, best_pair, 0, s->span_pair, st) != cudaSuccess) result = MD_ERR_CUDA;
+  if (result == MD_OK && launch_pair(s->a, best_pair, 0, st) != cudaSuccess) result = MD_ERR_CUDA;
   if (result == MD_OK && s->n_bonds > 0 && launch_bonds(s->a, 0, st) != cudaSuccess) result = MD_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) result = MD_ERR_CUDA;
   cudaEventDestroy(e0);

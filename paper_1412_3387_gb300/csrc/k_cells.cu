@@ -137,6 +137,7 @@ __global__ void k_bin_scatter(KArgs a, int force) {
   if (!rebuilding(a, r, force)) return;
   const Rep &rp = a.rep[r];
   a.cell_idx[a.cell_start[a.pcell[i]] + a.pslot[i]] = (int32_t)i;
+  if (i == rp.p0) a.ident[r] = 0;  // the new binning is not in particle order
   double4 x = ld_d4(a.pos + i);
   int cx = cell_coord(x.x, rp.inv_h[0], rp.nc[0]);
   int cy = cell_coord(x.y, rp.inv_h[1], rp.nc[1]);
@@ -216,6 +217,7 @@ __global__ void k_sort_scatter(KArgs a) {
   if (a.vel4f) a.vel4f[k] = a.s_vel4f[k];
   a.rtag[t] = (int32_t)k;
   a.cell_idx[k] = (int32_t)k;  // the cell list order is now the particle order
+  if (k == a.rep[r].p0) a.ident[r] = 1;
 }
 
 inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }

@@ -320,14 +320,33 @@ __global__ void k_export_forces(KArgs a, double *f, double *v) {
   }
 }
 
+// One warp per home cell: decode each row's stage slots into particle indices
+// and write them at the particle's own row.
 __global__ void k_export_nlist(KArgs a, int32_t *counts, int32_t *rows) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  const int nn = a.n_nb[i];
-  counts[i] = nn;
-  for (int k = 0; k < a.max_nb; k++)
-    rows[i * a.max_nb + k] =
-        k < nn ? (int32_t)(a.nl[nl_addr(i, k, a.w_store_log2, a.n_pad)] & kIdxMask) : -1;
+  __shared__ StageInfo si;
+  const int lane = threadIdx.x & 31;
+  const int64_t g = blockIdx.x;
+  const int cnt = a.cell_count[g];
+  if (cnt == 0) return;
+  const Rep &rp = a.rep[a.chunk_rep[g / kChunkCells]];
+  stage_info(a, rp, g, si);
+  __syncthreads();
+  const int start = a.cell_start[g];
+  for (int q = 0; q < cnt; q++) {
+    const int p = start + q;
+    const int32_t i = a.cell_idx[p];
+    const int nn = a.n_nb[p];
+    if (lane == 0) counts[i] = nn;
+    for (int k = lane; k < a.max_nb; k += 32) {
+      int32_t j = -1;
+      if (k < nn) {
+        const int slot = a.nl[nl_addr(p, k, a.w_store_log2, a.n_pad)];
+        const int s = stage_cell(si, slot);
+        j = a.cell_idx[si.start[s] + (slot - si.off[s])];
+      }
+      rows[(int64_t)i * a.max_nb + k] = j;
+    }
+  }
 }
 
 __global__ void k_export_cells(KArgs a, int32_t *start, int32_t *count, int32_t *idx) {
@@ -399,7 +418,7 @@ cudaError_t launch_export_forces(const KArgs &a, double *f, double *v, cudaStrea
 
 cudaError_t launch_export_nlist(const KArgs &a, int32_t *counts, int32_t *rows, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  k_export_nlist<<<blocks_for(a.n, 256), 256, 0, st>>>(a, counts, rows);
+  k_export_nlist<<<(unsigned)a.n_cells, 32, 0, st>>>(a, counts, rows);
   return cudaGetLastError();
 }
 

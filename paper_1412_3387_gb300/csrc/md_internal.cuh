@@ -97,8 +97,9 @@ struct KArgs {
   int32_t *cell_idx;   // [N]
   int32_t *pcell;      // [N] cell slot of each particle (binning)
   int32_t *pslot;      // [N] rank inside its cell (binning)
-  uint32_t *nl;        // [max_nb * n_pad]
-  int32_t *n_nb;       // [N]
+  uint16_t *nl;        // [max_nb * n_pad] stage slots, rows indexed by cell position
+  int32_t *n_nb;       // [n_pad] row lengths, indexed by cell position
+  int32_t stage_cap;   // stage slots per warp (pair / list kernels)
   void *force;         // double4[N] (FP64) or float4[N] (mixed)
   void *virial;        // double[N][6] or float[N][6]
   double *tpart;       // [thermo chunks][8]
@@ -107,6 +108,7 @@ struct KArgs {
   int32_t *sort_now;   // [R]
   int64_t *last_sort;  // [R]
   int32_t *rtag;       // [N] tag -> index
+  int32_t *ident;      // [R] 1 while the replica's particles are in cell order
   int32_t *btab;       // [N][max_bonds] partner tags (-1 = none)
   // sort scratch
   double4 *s_pos, *s_vel;
@@ -192,7 +194,111 @@ __device__ __forceinline__ double4 ld_d4(const double4 *p) {
   return make_double4(a.x, a.y, b.x, b.y);
 }
 
-// Neighbour-list address of entry k of row i for tile width 2^lw.
+// ---- cell stage ------------------------------------------------------------
+// The stage of home cell g is the concatenation, in ascending Hilbert rank,
+// of the members of the 27 cells around g (g included).  Slot s holds the
+// member's FP32 frame offset plus the offset d h of its cell relative to g
+// (d in {-1,0,1}^3), so that x_i - x_j = o_i - stage[s] for a home particle
+// i.  Rows of the neighbour list hold stage slots (16 bits: a stage has at
+// most 27 x kMaxCellSort slots).  A block stages at most `stage_cap` slots at
+// a time; denser neighbourhoods are processed in windows of that size (rows
+// are in ascending slot order, so each window is a contiguous part of a row).
+struct StageInfo {
+  int off[28];          // first slot of each stencil cell; off[27] = total
+  int start[27];        // cell_start of each stencil cell
+  float sx[27], sy[27], sz[27];  // image shift d h of each stencil cell
+  int self;             // first slot of the home cell's own members
+  int pad[3];
+};
+
+// Filled by the first warp of the block (lanes 0..26: one stencil cell each);
+// the caller synchronises the block before use.
+__device__ __forceinline__ void stage_info(const KArgs &a, const Rep &rp, int64_t g, StageInfo &si) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32) return;
+  int cnt = 0, code = -1;
+  if (lane < 27) {
+    const uint32_t e = __ldg(a.stencil + g * 27 + lane);
+    const int64_t cell = rp.cell0 + (int64_t)(e & kIdxMask);
+    code = (int)(e >> kIdxBits);
+    cnt = __ldg(a.cell_count + cell);
+    si.start[lane] = __ldg(a.cell_start + cell);
+    si.sx[lane] = (float)(code % 3 - 1) * rp.hf[0];
+    si.sy[lane] = (float)((code / 3) % 3 - 1) * rp.hf[1];
+    si.sz[lane] = (float)(code / 9 - 1) * rp.hf[2];
+  }
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane < 27) si.off[lane] = incl - cnt;
+  if (lane == 26) si.off[27] = incl;
+  if (code == 13) si.self = incl - cnt;
+}
+
+// Stencil cell holding stage slot `slot` (largest s with off[s] <= slot).
+__device__ __forceinline__ int stage_cell(const StageInfo &si, int slot) {
+  int s = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1)
+    if (s + step < 27 && si.off[s + step] <= slot) s += step;
+  return s;
+}
+
+// Fills window slots [w0, w0 + m) of the stage with all threads of the block:
+// positions (pre-shifted), and particle indices / FP32 velocities when idx /
+// vel are given.  Each thread takes slots tid, tid + blockDim, ...; kUnroll of
+// them are looked up and loaded independently before any is stored, so a
+// stage costs about one memory latency.  When the replica's particles are in
+// cell order (`ident`: after each space-filling-curve sort, until the next
+// binning) cell members are index ranges and the cell_idx lookup is skipped.
+// The caller synchronises the block before and after.
+__device__ __forceinline__ void stage_fill(const KArgs &a, const StageInfo &si, int w0, int m,
+                                           bool ident, float4 *pos, int32_t *idx, float4 *vel) {
+  constexpr int kUnroll = 4;
+  const int nt = blockDim.x;
+  for (int b = 0; b < m; b += nt * kUnroll) {
+    int32_t j[kUnroll];
+    int sc[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      const int k = b + u * nt + threadIdx.x;
+      j[u] = -1;
+      sc[u] = 0;
+      if (k < m) {
+        const int slot = w0 + k;
+        const int s = stage_cell(si, slot);
+        sc[u] = s;
+        const int at = si.start[s] + (slot - si.off[s]);
+        j[u] = ident ? at : __ldg(a.cell_idx + at);
+      }
+    }
+    float4 o[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++)
+      o[u] = j[u] >= 0 ? __ldg(a.pos4f + j[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      if (j[u] < 0) continue;
+      const int k = b + u * nt + threadIdx.x;
+      const int s = sc[u];
+      pos[k] = make_float4(o[u].x + si.sx[s], o[u].y + si.sy[s], o[u].z + si.sz[s], o[u].w);
+      if (idx) idx[k] = j[u];
+      if (vel) vel[k] = __ldg(a.vel4f + j[u]);
+    }
+  }
+}
+
+// Shared memory of one block: StageInfo, then stage_cap slots of positions,
+// indices and (DPD) velocities.
+__host__ __device__ __forceinline__ size_t stage_bytes(int cap, bool with_vel) {
+  return sizeof(StageInfo) + (size_t)cap * (sizeof(float4) + sizeof(int32_t)) +
+         (with_vel ? (size_t)cap * sizeof(float4) : 0);
+}
+
+// Neighbour-list address of entry k of row p for tile width 2^lw.
 __device__ __forceinline__ size_t nl_addr(int64_t i, int k, int lw, int64_t n_pad) {
   return ((((size_t)(k >> lw)) * (size_t)n_pad + (size_t)i) << lw) | (size_t)(k & ((1 << lw) - 1));
 }
@@ -232,8 +338,9 @@ cudaError_t launch_integrate2(const KArgs &a, cudaStream_t st);
 cudaError_t launch_bin(const KArgs &a, int force, cudaStream_t st);
 cudaError_t launch_sort(const KArgs &a, int force, cudaStream_t st);
 cudaError_t launch_nlist(const KArgs &a, Launch l, int force, cudaStream_t st);
-cudaError_t launch_pair_span(const KArgs &a, Launch l, int want_virial, int span, cudaStream_t st);
-int pair_span(const int64_t *off, int R, int64_t n, int per_block);
+cudaError_t launch_pair(const KArgs &a, Launch l, int want_virial, cudaStream_t st);
+void pair_init_attributes();
+void nlist_init_attributes();
 cudaError_t launch_bonds(const KArgs &a, int want_virial, cudaStream_t st);
 cudaError_t launch_thermo(const KArgs &a, double *out, int from_run, cudaStream_t st);
 cudaError_t launch_set_step(const KArgs &a, int64_t step, cudaStream_t st);
@@ -247,7 +354,7 @@ cudaError_t launch_export_cells(const KArgs &a, int32_t *start, int32_t *count, 
                                 cudaStream_t st);
 cudaError_t launch_philox(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t st);
 cudaError_t launch_init_frames(const KArgs &a, cudaStream_t st);
-int max_block_nlist(int w);
+int max_block_nlist(int w, int cap);
 int max_block_pair(const KArgs &a, int w, int want_virial);
 
 }  // namespace mdgb
