@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 1
+#define MD_ABI_VERSION 2
 
 typedef struct md_system md_system;
 typedef struct CUstream_st *md_stream; /* a cudaStream_t; NULL = legacy default stream */
@@ -49,7 +49,8 @@ typedef enum {
     MD_ERR_CELL_GRID = 5,            /* fewer than 3 cells per box edge */
     MD_ERR_NONFINITE = 6,            /* non-finite position after integration */
     MD_ERR_CELL_OVERFLOW = 7,        /* a cell held more particles than can be ordered */
-    MD_ERR_STATE = 8                 /* call not valid in the current state */
+    MD_ERR_STATE = 8,                /* call not valid in the current state */
+    MD_ERR_TIMEOUT = 9               /* a kernel's internal wait gave up (an internal error) */
 } md_status;
 
 typedef enum { MD_FP64 = 0, MD_MIXED = 1 } md_precision;
@@ -186,15 +187,22 @@ md_status md_reduce_thermo(md_system *s, double *dev_out, md_stream stream);
 md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream stream);
 
 /* Autotuner (Sec. 5.2): for the pair and neighbour-list kernels, times every
- * (block size b = 32 k <= 1024, threads per particle w = 2^m <= 32) pair,
- * b >= w, with the median of n_samples launches (paper: 5), and keeps the
- * fastest.  block_stride (>= 1) thins the block sizes to every block_stride-th
- * multiple of 32.  Synchronises `stream`; rebuilds the neighbour list. */
+ * (block size b = 32 k <= 512, threads per particle w = 2^m <= 32) pair with
+ * the median of n_samples launches (paper: 5), and keeps the fastest.  Both
+ * kernels are persistent and b counts their computing threads (each block has
+ * one more warp that streams data into shared memory).  The list build's w is
+ * at most the pair kernel's (the pair kernel's w fixes the list layout, and a
+ * build pass must cover whole row groups of it).  block_stride (>= 1) thins
+ * the block sizes to every block_stride-th multiple of 32.  Synchronises
+ * `stream`; rebuilds the neighbour list. */
 md_status md_autotune(md_system *s, int32_t n_samples, int32_t block_stride,
                       md_stream stream);
 
-/* Sets / reads the launch parameters of one kernel (md_kernel).  Changing the
- * pair kernel's w changes the list layout and forces a rebuild. */
+/* Sets / reads the launch parameters of one kernel (md_kernel): b computing
+ * threads (a multiple of 32, at most the kernel's limit) and w threads per
+ * particle.  Changing the pair kernel's w changes the list layout and forces
+ * a rebuild; a list-build w above the pair kernel's runs at the pair
+ * kernel's. */
 md_status md_set_tuning(md_system *s, int32_t kernel, int32_t block, int32_t w);
 md_status md_get_tuning(md_system *s, int32_t kernel, int32_t *block, int32_t *w);
 

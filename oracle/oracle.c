@@ -511,14 +511,18 @@ void orc_sfc_order(int64_t n, const double *pos, const double *L, double r_list,
         if (nc[k] == 0) nc[k] = 1;
         if (nc[k] > nmax) nmax = nc[k];
     }
+    /* the curve runs over bricks of 2 x 2 x 2 cells (ceil(nc / 2) per edge);
+     * inside a brick the cells go x first, then y, then z */
+    int32_t bmax = (nmax + 1) / 2;
     int32_t bits = 1;
-    while ((1 << bits) < nmax) bits++;
-    /* bits >= 1 even for a single cell per edge */
+    while ((1 << bits) < bmax) bits++;
+    /* bits >= 1 even for a single brick per edge */
     keyidx_t *ki = malloc(sizeof(keyidx_t) * (size_t)(n > 0 ? n : 1));
     for (int64_t i = 0; i < n; i++) {
         uint32_t c[3];
         for (int k = 0; k < 3; k++) c[k] = (uint32_t)cell_of(pos[4 * i + k], nc[k], L[k]);
-        ki[i].key = orc_hilbert3(c[0], c[1], c[2], bits);
+        const uint64_t brick = orc_hilbert3(c[0] >> 1, c[1] >> 1, c[2] >> 1, bits);
+        ki[i].key = brick * 8u + (c[0] & 1u) + 2u * (c[1] & 1u) + 4u * (c[2] & 1u);
         ki[i].idx = i;
     }
     qsort(ki, (size_t)n, sizeof(keyidx_t), cmp_keyidx);

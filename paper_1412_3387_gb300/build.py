@@ -17,7 +17,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmdgb.so")
-SOURCES = ["api.cu", "k_cells.cu", "k_nlist.cu", "k_pair.cu", "k_integrate.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "k_cells.cu", "k_nlist.cu", "k_pair.cu", "k_pair_lj_mixed.cu",
+           "k_pair_lj_fp64.cu", "k_pair_dpd_mixed.cu", "k_pair_dpd_fp64.cu", "k_integrate.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -42,7 +44,9 @@ def _stale(out: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "md_internal.cuh"), os.path.join(ROOT, "include", "md.h"),
+    headers = [os.path.join(CSRC, "md_internal.cuh"), os.path.join(CSRC, "brick.cuh"),
+               os.path.join(CSRC, "pair_impl.cuh"),
+               os.path.join(ROOT, "include", "md.h"),
                os.path.abspath(__file__)]
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "md_internal.cuh"
+#include "brick.cuh"
 
 using namespace mdgb;
 
@@ -22,7 +23,7 @@ struct md_system {
   md_particles parts{};
   KArgs a{};
   std::vector<Rep> reps;
-  Launch tune[2]{{128, 1}, {128, 1}};  // nlist, pair
+  Launch tune[2]{{128, 2}, {128, 2}};  // nlist, pair (computing threads, w)
   bool built = false;   // list built and forces computed (ready to step)
   bool binned = false;  // cells binned at least once
   bool listed = false;  // list built in the current layout
@@ -42,6 +43,8 @@ namespace {
   } while (0)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+constexpr int kMaxTuneBlock = 512;  // largest computing-thread count the tuner tries
 
 int ilog2(int w) { int l = 0; while ((1 << l) < w) l++; return l; }
 
@@ -80,11 +83,13 @@ struct Plan {
   int64_t n = 0, n_pad = 0, n_cells = 0, n_chunks = 0, n_tchunks = 0;
   int32_t max_nb = 0;
   int32_t stage_cap = 0;
+  int64_t n_bricks = 0;
   // byte offsets into the workspace
-  size_t o_rep, o_off, o_chunk_rep, o_tchunk_rep, o_cell_rank, o_stencil, o_cell_count, o_cell_start,
-      o_chunk_sum, o_cell_idx, o_pcell, o_pslot, o_n_nb, o_rtag, o_pos4f, o_oref, o_vel4f, o_nl,
-      o_force, o_virial, o_tpart, o_ds, o_rebuild, o_sort_now, o_last_sort, o_ident, o_coeff, o_btab,
-      o_s_pos, o_s_vel, o_s_img, o_s_tag, o_s_type, o_s_pos4f, o_s_oref, o_s_vel4f;
+  size_t o_rep, o_off, o_chunk_rep, o_tchunk_rep, o_cell_rank, o_brick_stage, o_brick_info,
+      o_brick_rep, o_brick_desc, o_cell_count, o_cell_start,
+      o_chunk_sum, o_cell_idx, o_cellpos, o_pcell, o_pslot, o_n_nb, o_rtag, o_pos4f, o_oref, o_vel4f,
+      o_nl, o_nl_tiles, o_force, o_virial, o_tpart, o_ds, o_rebuild, o_sort_now, o_last_sort, o_ident,
+      o_list_ok, o_coeff, o_btab, o_s_pos, o_s_vel, o_s_img, o_s_tag, o_s_type, o_s_oref;
   size_t total = 0;
 };
 
@@ -156,18 +161,27 @@ md_status make_plan(const md_params *p, Plan &pl) {
     rp.cell0 = cell0;
     rp.chunk0 = chunk0;
     rp.tchunk0 = tchunk0;
+    rp.brick0 = pl.n_bricks;
+    rp.nbrick = ((rp.nc[0] + 1) / 2) * ((rp.nc[1] + 1) / 2) * ((rp.nc[2] + 1) / 2);
+    pl.n_bricks += rp.nbrick;
     cell0 += (int64_t)rp.nchunk * kChunkCells;
     chunk0 += rp.nchunk;
     tchunk0 += rp.ntchunk;
   }
-  // stage capacity per warp: 15 % above the mean stencil population of the
-  // densest replica (denser neighbourhoods are processed in windows)
+  // Brick stage buffers (brick.cuh): room for about 20 % more than the mean
+  // population of the 64 stage cells of the densest replica; a brick beyond
+  // that is served from global memory instead.  Two buffers (positions, and
+  // velocities for mixed-precision DPD) must fit well inside shared memory.
   double dens = 0.0;
   for (const Rep &rp : pl.reps)
     if (rp.ncell > 0) dens = std::max(dens, (double)(rp.p1 - rp.p0) / rp.ncell);
-  int cap = (int)std::ceil((1.15 * 27.0 * dens + 32.0) / 32.0) * 32;
-  pl.stage_cap = std::min(std::max(cap, 128), 27 * kMaxCellSort);
+  const bool vel = p->pair == MD_PAIR_DPD && p->precision == MD_MIXED;
+  int cap = (int)std::ceil((1.2 * 64.0 * dens + 64.0) / 32.0) * 32;
+  cap = std::min(cap, 64 * kMaxCellSort);
+  while (BrickSmem::bytes(cap, vel, 0) > 160u * 1024u) cap /= 2;
+  pl.stage_cap = std::max(cap, 32);
   pl.n_cells = cell0;
+  if (pl.n_cells > (int64_t)INT32_MAX) return MD_ERR_CELL_GRID;
   pl.n_chunks = chunk0;
   pl.n_tchunks = tchunk0;
   const bool mixed = p->precision == MD_MIXED;
@@ -180,11 +194,15 @@ md_status make_plan(const md_params *p, Plan &pl) {
   pl.o_chunk_rep = take(sizeof(int32_t) * pl.n_chunks);
   pl.o_tchunk_rep = take(sizeof(int32_t) * pl.n_tchunks);
   pl.o_cell_rank = take(sizeof(int32_t) * pl.n_cells);
-  pl.o_stencil = take(sizeof(uint32_t) * 27 * (size_t)pl.n_cells);
+  pl.o_brick_stage = take(sizeof(int32_t) * kStageCells * (size_t)pl.n_bricks);
+  pl.o_brick_info = take(sizeof(int4) * (size_t)pl.n_bricks);
+  pl.o_brick_rep = take(sizeof(int32_t) * (size_t)pl.n_bricks);
+  pl.o_brick_desc = take(sizeof(BrickDesc) * (size_t)pl.n_bricks);
   pl.o_cell_count = take(sizeof(int32_t) * pl.n_cells);
   pl.o_cell_start = take(sizeof(int32_t) * pl.n_cells);
   pl.o_chunk_sum = take(sizeof(int32_t) * pl.n_chunks);
   pl.o_cell_idx = take(sizeof(int32_t) * N);
+  pl.o_cellpos = take(sizeof(int32_t) * N);
   pl.o_pcell = take(sizeof(int32_t) * N);
   pl.o_pslot = take(sizeof(int32_t) * N);
   pl.o_n_nb = take(sizeof(int32_t) * NP);
@@ -193,6 +211,7 @@ md_status make_plan(const md_params *p, Plan &pl) {
   pl.o_oref = take(sizeof(float4) * NP);
   pl.o_vel4f = dpd ? take(sizeof(float4) * NP) : 0;
   pl.o_nl = take(sizeof(uint16_t) * (size_t)pl.max_nb * NP);
+  pl.o_nl_tiles = take(sizeof(int32_t) * NP);
   pl.o_force = take((mixed ? sizeof(float4) : sizeof(double4)) * NP);
   pl.o_virial = take((mixed ? sizeof(float) : sizeof(double)) * 6 * NP);
   pl.o_tpart = take(sizeof(double) * 8 * pl.n_tchunks);
@@ -201,6 +220,7 @@ md_status make_plan(const md_params *p, Plan &pl) {
   pl.o_sort_now = take(sizeof(int32_t) * R);
   pl.o_last_sort = take(sizeof(int64_t) * R);
   pl.o_ident = take(sizeof(int32_t) * R);
+  pl.o_list_ok = take(sizeof(int32_t) * R);
   pl.o_coeff = take(64 * (size_t)p->n_types * p->n_types);
   pl.o_btab = take(sizeof(int32_t) * (size_t)std::max(p->max_bonds, 0) * N);
   pl.o_s_pos = take(sizeof(double4) * N);
@@ -208,9 +228,7 @@ md_status make_plan(const md_params *p, Plan &pl) {
   pl.o_s_img = take(sizeof(int4) * N);
   pl.o_s_tag = take(sizeof(int32_t) * N);
   pl.o_s_type = take(sizeof(int32_t) * N);
-  pl.o_s_pos4f = take(sizeof(float4) * N);
   pl.o_s_oref = take(sizeof(float4) * N);
-  pl.o_s_vel4f = dpd ? take(sizeof(float4) * N) : 0;
   pl.total = o;
   return MD_OK;
 }
@@ -255,6 +273,26 @@ bool valid_launch(int block, int w) {
 
 }  // namespace
 
+namespace mdgb {
+
+int persistent_grid(const void *kernel, int threads, size_t smem, int64_t work) {
+  static int dev = -1, nsm = 0;
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) return 0;
+  if (d != dev) {
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) return 0;
+    dev = d;
+  }
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess)
+    return 0;
+  if (per <= 0) return 0;
+  const int64_t g = std::min<int64_t>((int64_t)per * nsm, std::max<int64_t>(work, 1));
+  return (int)g;
+}
+
+}  // namespace mdgb
+
 extern "C" {
 
 int32_t md_abi_version(void) { return MD_ABI_VERSION; }
@@ -270,6 +308,7 @@ const char *md_status_string(md_status s) {
     case MD_ERR_NONFINITE: return "non-finite particle position";
     case MD_ERR_CELL_OVERFLOW: return "cell occupancy above the in-cell sort limit";
     case MD_ERR_STATE: return "call not valid in the current state";
+    case MD_ERR_TIMEOUT: return "a kernel's internal wait timed out (internal error)";
   }
   return "unknown status";
 }
@@ -339,14 +378,19 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   a.oref = at<float4>(ws, pl.o_oref);
   a.vel4f = dpd ? at<float4>(ws, pl.o_vel4f) : nullptr;
   a.cell_rank = at<int32_t>(ws, pl.o_cell_rank);
-  a.stencil = at<uint32_t>(ws, pl.o_stencil);
+  a.brick_stage = at<int32_t>(ws, pl.o_brick_stage);
+  a.brick_info = at<int4>(ws, pl.o_brick_info);
+  a.brick_rep = at<int32_t>(ws, pl.o_brick_rep);
+  a.brick_desc = at<BrickDesc>(ws, pl.o_brick_desc);
   a.cell_count = at<int32_t>(ws, pl.o_cell_count);
   a.cell_start = at<int32_t>(ws, pl.o_cell_start);
   a.chunk_sum = at<int32_t>(ws, pl.o_chunk_sum);
   a.cell_idx = at<int32_t>(ws, pl.o_cell_idx);
+  a.cellpos = at<int32_t>(ws, pl.o_cellpos);
   a.pcell = at<int32_t>(ws, pl.o_pcell);
   a.pslot = at<int32_t>(ws, pl.o_pslot);
   a.nl = at<uint16_t>(ws, pl.o_nl);
+  a.nl_tiles = at<int32_t>(ws, pl.o_nl_tiles);
   a.stage_cap = pl.stage_cap;
   a.n_nb = at<int32_t>(ws, pl.o_n_nb);
   a.force = at<void>(ws, pl.o_force);
@@ -357,6 +401,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   a.sort_now = at<int32_t>(ws, pl.o_sort_now);
   a.last_sort = at<int64_t>(ws, pl.o_last_sort);
   a.ident = at<int32_t>(ws, pl.o_ident);
+  a.list_ok = at<int32_t>(ws, pl.o_list_ok);
   a.rtag = at<int32_t>(ws, pl.o_rtag);
   a.btab = p->max_bonds > 0 ? at<int32_t>(ws, pl.o_btab) : nullptr;
   a.s_pos = at<double4>(ws, pl.o_s_pos);
@@ -364,9 +409,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   a.s_img = at<int4>(ws, pl.o_s_img);
   a.s_tag = at<int32_t>(ws, pl.o_s_tag);
   a.s_type = at<int32_t>(ws, pl.o_s_type);
-  a.s_pos4f = at<float4>(ws, pl.o_s_pos4f);
   a.s_oref = at<float4>(ws, pl.o_s_oref);
-  a.s_vel4f = dpd ? at<float4>(ws, pl.o_s_vel4f) : nullptr;
   a.coeff = at<void>(ws, pl.o_coeff);
   a.max_nb = pl.max_nb;
   a.sort_period = p->sort_period;
@@ -388,42 +431,62 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   a.n_chunks = pl.n_chunks;
   a.n_tchunks = pl.n_tchunks;
   a.n_cells = pl.n_cells;
+  a.n_bricks = pl.n_bricks;
 
-  // host tables
+  // host tables: cell ranks (bricks of 2 x 2 x 2 cells along a Hilbert curve,
+  // the cells of a brick x first, then y, then z) and per brick its 64 stage
+  // cells and its own cells
   std::vector<int32_t> chunk_rep(pl.n_chunks), tchunk_rep(pl.n_tchunks);
   std::vector<int32_t> rank(pl.n_cells, 0);
-  std::vector<uint32_t> stencil((size_t)pl.n_cells * 27, 0);
+  std::vector<int32_t> bstage((size_t)pl.n_bricks * kStageCells, 0);
+  std::vector<int4> binfo((size_t)pl.n_bricks);
+  std::vector<int32_t> brep((size_t)pl.n_bricks, 0);
   for (int r = 0; r < R; r++) {
     const Rep &rp = pl.reps[r];
     for (int c = 0; c < rp.nchunk; c++) chunk_rep[rp.chunk0 + c] = r;
     for (int c = 0; c < rp.ntchunk; c++) tchunk_rep[rp.tchunk0 + c] = r;
-    const int nmax = std::max(rp.nc[0], std::max(rp.nc[1], rp.nc[2]));
+    const int nb[3] = {(rp.nc[0] + 1) / 2, (rp.nc[1] + 1) / 2, (rp.nc[2] + 1) / 2};
+    const int nmax = std::max(nb[0], std::max(nb[1], nb[2]));
     int bits = 1;
     while ((1 << bits) < nmax) bits++;
-    std::vector<std::pair<uint64_t, int32_t>> keys(rp.ncell);
-    for (int z = 0; z < rp.nc[2]; z++)
-      for (int y = 0; y < rp.nc[1]; y++)
-        for (int x = 0; x < rp.nc[0]; x++) {
-          const int32_t lin = x + rp.nc[0] * (y + rp.nc[1] * z);
+    std::vector<std::pair<uint64_t, int32_t>> keys((size_t)rp.nbrick);
+    for (int z = 0; z < nb[2]; z++)
+      for (int y = 0; y < nb[1]; y++)
+        for (int x = 0; x < nb[0]; x++) {
+          const int32_t lin = x + nb[0] * (y + nb[1] * z);
           keys[lin] = {hilbert_key(x, y, z, bits), lin};
         }
     std::sort(keys.begin(), keys.end());
-    for (int32_t k = 0; k < rp.ncell; k++) rank[rp.cell0 + keys[k].second] = k;
-    // for every cell (by rank): its 27 neighbours (periodic), ascending rank,
-    // each tagged with the code (dx+1) + 3 (dy+1) + 9 (dz+1) of its offset
-    for (int32_t k = 0; k < rp.ncell; k++) {
-      const int32_t lin = keys[k].second;
-      const int x = lin % rp.nc[0], y = (lin / rp.nc[0]) % rp.nc[1], z = lin / (rp.nc[0] * rp.nc[1]);
-      uint32_t nb[27];
-      for (int code = 0; code < 27; code++) {
-        const int nx = (x + code % 3 - 1 + rp.nc[0]) % rp.nc[0];
-        const int ny = (y + (code / 3) % 3 - 1 + rp.nc[1]) % rp.nc[1];
-        const int nz = (z + code / 9 - 1 + rp.nc[2]) % rp.nc[2];
-        const int32_t nlin = nx + rp.nc[0] * (ny + rp.nc[1] * nz);
-        nb[code] = (uint32_t)rank[rp.cell0 + nlin] | ((uint32_t)code << kIdxBits);
+    auto cell_lin = [&](int x, int y, int z) {
+      x = ((x % rp.nc[0]) + rp.nc[0]) % rp.nc[0];
+      y = ((y % rp.nc[1]) + rp.nc[1]) % rp.nc[1];
+      z = ((z % rp.nc[2]) + rp.nc[2]) % rp.nc[2];
+      return x + rp.nc[0] * (y + rp.nc[1] * z);
+    };
+    int32_t k = 0;
+    for (int64_t bi = 0; bi < rp.nbrick; bi++) {
+      const int32_t lin = keys[bi].second;
+      const int bx = lin % nb[0], by = (lin / nb[0]) % nb[1], bz = lin / (nb[0] * nb[1]);
+      const int64_t B = rp.brick0 + bi;
+      int mask = 0;
+      const int32_t first = k;
+      for (int q = 0; q < 8; q++) {
+        const int x = 2 * bx + (q & 1), y = 2 * by + ((q >> 1) & 1), z = 2 * bz + (q >> 2);
+        if (x >= rp.nc[0] || y >= rp.nc[1] || z >= rp.nc[2]) continue;
+        rank[rp.cell0 + cell_lin(x, y, z)] = k++;
+        mask |= 1 << q;
       }
-      std::sort(nb, nb + 27, [](uint32_t u, uint32_t v) { return (u & kIdxMask) < (v & kIdxMask); });
-      std::copy(nb, nb + 27, stencil.begin() + (size_t)(rp.cell0 + k) * 27);
+      binfo[B] = make_int4((int)(rp.cell0 + first), mask, r, 0);
+      brep[B] = r;
+    }
+    for (int64_t bi = 0; bi < rp.nbrick; bi++) {
+      const int32_t lin = keys[bi].second;
+      const int bx = lin % nb[0], by = (lin / nb[0]) % nb[1], bz = lin / (nb[0] * nb[1]);
+      const int64_t B = rp.brick0 + bi;
+      for (int s = 0; s < kStageCells; s++) {
+        const int x = 2 * bx - 1 + (s & 3), y = 2 * by - 1 + ((s >> 2) & 3), z = 2 * bz - 1 + (s >> 4);
+        bstage[(size_t)B * kStageCells + s] = (int32_t)(rp.cell0 + rank[rp.cell0 + cell_lin(x, y, z)]);
+      }
     }
   }
   std::vector<unsigned char> coeff(64 * (size_t)p->n_types * p->n_types, 0);
@@ -463,12 +526,16 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
       cudaMemcpyAsync(at<void>(ws, pl.o_chunk_rep), chunk_rep.data(), sizeof(int32_t) * pl.n_chunks, cudaMemcpyHostToDevice, stream) ||
       cudaMemcpyAsync(at<void>(ws, pl.o_tchunk_rep), tchunk_rep.data(), sizeof(int32_t) * pl.n_tchunks, cudaMemcpyHostToDevice, stream) ||
       cudaMemcpyAsync(at<void>(ws, pl.o_cell_rank), rank.data(), sizeof(int32_t) * pl.n_cells, cudaMemcpyHostToDevice, stream) ||
-      cudaMemcpyAsync(at<void>(ws, pl.o_stencil), stencil.data(), sizeof(uint32_t) * stencil.size(), cudaMemcpyHostToDevice, stream) ||
+      cudaMemcpyAsync(at<void>(ws, pl.o_brick_stage), bstage.data(), sizeof(int32_t) * bstage.size(), cudaMemcpyHostToDevice, stream) ||
+      cudaMemcpyAsync(at<void>(ws, pl.o_brick_info), binfo.data(), sizeof(int4) * binfo.size(), cudaMemcpyHostToDevice, stream) ||
+      cudaMemcpyAsync(at<void>(ws, pl.o_brick_rep), brep.data(), sizeof(int32_t) * brep.size(), cudaMemcpyHostToDevice, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_brick_desc), 0, sizeof(BrickDesc) * (size_t)pl.n_bricks, stream) ||
       cudaMemcpyAsync(at<void>(ws, pl.o_coeff), coeff.data(), coeff.size(), cudaMemcpyHostToDevice, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_cell_count), 0, sizeof(int32_t) * pl.n_cells, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_cell_start), 0, sizeof(int32_t) * pl.n_cells, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_n_nb), 0, sizeof(int32_t) * pl.n_pad, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_nl), 0, sizeof(uint16_t) * (size_t)pl.max_nb * pl.n_pad, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_nl_tiles), 0, sizeof(int32_t) * pl.n_pad, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_rtag), 0, sizeof(int32_t) * pl.n, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_pcell), 0, sizeof(int32_t) * pl.n, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_pslot), 0, sizeof(int32_t) * pl.n, stream) ||
@@ -478,7 +545,8 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
       cudaMemsetAsync(at<void>(ws, pl.o_rebuild), 0, sizeof(int32_t) * 2 * R, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_sort_now), 0, sizeof(int32_t) * R, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_last_sort), 0, sizeof(int64_t) * R, stream) ||
-      cudaMemsetAsync(at<void>(ws, pl.o_ident), 0, sizeof(int32_t) * R, stream))
+      cudaMemsetAsync(at<void>(ws, pl.o_ident), 0, sizeof(int32_t) * R, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_list_ok), 0, sizeof(int32_t) * R, stream))
     return fail(MD_ERR_CUDA);
   if (p->max_bonds > 0 &&
       cudaMemsetAsync(at<void>(ws, pl.o_btab), 0xff, sizeof(int32_t) * (size_t)p->max_bonds * pl.n, stream))
@@ -652,7 +720,7 @@ md_status md_set_tuning(md_system *s, int32_t kernel, int32_t block, int32_t w) 
   if (!s || (kernel != MD_KERNEL_NLIST && kernel != MD_KERNEL_PAIR) || !valid_launch(block, w))
     return MD_ERR_INVALID_ARG;
   const int mb = kernel == MD_KERNEL_NLIST
-                     ? max_block_nlist(w, s->a.stage_cap)
+                     ? max_block_nlist(s->a, w)
                      : std::min(max_block_pair(s->a, w, 0), max_block_pair(s->a, w, 1));
   if (block > mb) return MD_ERR_INVALID_ARG;
   if (kernel == MD_KERNEL_NLIST) {
@@ -705,8 +773,7 @@ md_status md_autotune(md_system *s, int32_t n_samples, int32_t block_stride, md_
     set_pair_w(s, Launch{std::max(32, w), w});
     if (launch_nlist(s->a, s->tune[MD_KERNEL_NLIST], 1, st) != cudaSuccess) { result = MD_ERR_CUDA; break; }
     const int mb = std::min(max_block_pair(s->a, w, 0), max_block_pair(s->a, w, 1));
-    for (int b = 32 * block_stride; b <= std::min(1024, mb); b += 32 * block_stride) {
-      if (b < w) continue;
+    for (int b = 32 * block_stride; b <= std::min(kMaxTuneBlock, mb); b += 32 * block_stride) {
       set_pair_w(s, Launch{b, w});
       const float t = median_time([&] { return launch_pair(s->a, Launch{b, w}, 0, st); });
       if (t < 0) { cudaGetLastError(); continue; }
@@ -719,9 +786,9 @@ md_status md_autotune(md_system *s, int32_t n_samples, int32_t block_stride, md_
   best_t = 1e30f;
   for (int w : ws) {
     if (result != MD_OK) break;
-    const int mb = max_block_nlist(w, s->a.stage_cap);
-    for (int b = 32 * block_stride; b <= std::min(1024, mb); b += 32 * block_stride) {
-      if (b < w) continue;
+    if (w > best_pair.w) break;  // the build's w is capped by the pair kernel's
+    const int mb = max_block_nlist(s->a, w);
+    for (int b = 32 * block_stride; b <= std::min(kMaxTuneBlock, mb); b += 32 * block_stride) {
       const float t = median_time([&] { return launch_nlist(s->a, Launch{b, w}, 1, st); });
       if (t < 0) { cudaGetLastError(); continue; }
       if (t < best_t) { best_t = t; best_nl = Launch{b, w}; }
@@ -767,6 +834,11 @@ md_status md_poll_error(md_system *s, int64_t *detail) {
     return MD_ERR_NONFINITE;
   }
   if (ds.error & kErrCellOverflow) return MD_ERR_CELL_OVERFLOW;
+  if (ds.error & kErrStaleList) return MD_ERR_STATE;
+  if (ds.error & kErrTimeout) {
+    if (detail) *detail = ds.error_detail;
+    return MD_ERR_TIMEOUT;
+  }
   return MD_OK;
 }
 

@@ -1,0 +1,252 @@
+// Brick stages shared by the neighbour-list build and the pair kernel.
+//
+// Cells are grouped into bricks of 2 x 2 x 2 (ceil(nc / 2) bricks per edge,
+// the last one thinner when nc is odd).  Bricks follow a Hilbert curve and a
+// brick's cells are consecutive in cell-list order (x first, then y, then z),
+// so a brick's particles are one contiguous range.
+//
+// The unit of work of both kernels is a brick.  Its stage is the 4 x 4 x 4
+// block of cells around it (stage cell s = sx + 4 sy + 16 sz covers cell
+// 2 b - 1 + s per axis, periodically wrapped; on very small grids a cell can
+// appear twice, at two periodic images).  Each home cell's 27 neighbour
+// cells form a 3 x 3 x 3 sub-block of the stage.  The stage holds the FP32
+// positions of all members of the 64 stage cells relative to the brick centre:
+// member offset from its own cell centre (pos4f, kept in cell-list order so
+// each cell is a contiguous range) plus (s - 1.5) h per axis.  Then
+//   x_i - x_j = stage[slot of i] - stage[slot of j]
+// for any home particle i and stage particle j of its stencil.
+//
+// A persistent block walks bricks b, b + G, b + 2G, ... with two stage
+// buffers: while its warps compute brick t, the 16-byte asynchronous copies
+// (cp.async) of brick t + 1's stage are in flight; after a block barrier the
+// warps add the shifts, and a second barrier publishes the stage.  A brick's
+// descriptor (stage layout: first slot and cell-list start of each stage
+// cell, home cells) is built once per binning (k_brick_desc) and read with one
+// coalesced load two bricks ahead.
+//
+// Stage slot 0 is a sentinel particle far away (its r^2 to anything
+// overflows to +inf, never inside a cut-off, and 0 * its offset is 0).  Row
+// entries are 1 + the slot index; rows are padded with 0.
+//
+// Row layout: a brick's particles form groups of P = 32 / W (W = the pair
+// kernel's lanes per particle; one group is one warp's work).  Group j
+// (particles jP .. jP + Pj - 1, at cell-list positions hstart + jP ...) keeps
+// its rows in the list region reserved for those particles, starting at
+// (hstart + jP) * max_nb, as T_j tiles: entry k of the group's particle q sits
+// at ((k / W) * Pj + q) * W + k % W, T_j = ceil(max row length / W), so a
+// warp's W lanes per particle read consecutive entries.
+//
+// A brick whose stage does not fit the buffer (an unusually dense region) is
+// "direct": its positions are read from global memory instead.
+#pragma once
+
+#include "md_internal.cuh"
+
+namespace mdgb {
+
+constexpr int kStageCells = 64;
+constexpr float kFar = 1e30f;  // sentinel coordinate
+constexpr int kMaxBrickThreads = 512;
+
+// Stage layout of one brick (global array, built per binning; copied to
+// shared memory by the kernels).  640 bytes.
+struct BrickDesc {
+  int off[65];    // first slot (0-based, sentinel excluded) of each stage cell; off[64] = total
+  int start[64];  // cell-list position of each stage cell's first member
+  int r;          // replica
+  int hstart;     // cell-list position of the brick's first particle
+  int nhome;      // particles in the brick
+  int hmask;      // bit p set if the brick's cell p = hx + 2 hy + 4 hz exists
+  int hoff[9];    // the brick's particle q lies in its i-th existing cell for hoff[i] <= q < hoff[i+1]
+  int hcell[8];   // stage cell of the brick's i-th existing cell
+  int hbase[8];   // staged slot of the particle at cell-list position p of that cell: p + hbase[i]
+  int pad[2];
+};
+static_assert(sizeof(BrickDesc) == 640, "BrickDesc layout");
+
+// Stage cell of the brick's i-th existing cell.
+__device__ __forceinline__ int home_stage_cell(int hmask, int i) {
+  int p = 0;
+  for (int k = 0, seen = 0; k < 8; k++)
+    if ((hmask >> k) & 1) {
+      if (seen == i) p = k;
+      seen++;
+    }
+  return (1 + (p & 1)) + 4 * (1 + ((p >> 1) & 1)) + 16 * (1 + (p >> 2));
+}
+
+// The brick's existing cell holding its particle q.
+__device__ __forceinline__ int home_cell_of(const BrickDesc &d, int q) {
+  int i = 0;
+#pragma unroll
+  for (int k = 1; k < 8; k++) i += d.hoff[k] <= q ? 1 : 0;
+  return i;
+}
+
+// Stage cell holding 0-based slot s (largest k with off[k] <= s).
+__device__ __forceinline__ int stage_cell_of(const BrickDesc &d, int s) {
+  int k = 0;
+#pragma unroll
+  for (int step = 32; step >= 1; step >>= 1)
+    if (k + step < kStageCells && d.off[k + step] <= s) k += step;
+  return k;
+}
+
+__device__ __forceinline__ float3 stage_shift(const Rep &rp, int s) {
+  return make_float3(((float)(s & 3) - 1.5f) * rp.hf[0], ((float)((s >> 2) & 3) - 1.5f) * rp.hf[1],
+                     ((float)(s >> 4) - 1.5f) * rp.hf[2]);
+}
+
+// ---- asynchronous copies (PTX) ---------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// 16-byte copy global -> shared, both 16-byte aligned, through L2 only.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Shared-memory accesses through 32-bit shared-window addresses: one 128-bit
+// load per staged particle, whatever the compiler can prove about a pointer.
+__device__ __forceinline__ float4 lds4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void sts16(uint32_t addr, uint16_t v) {
+  asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
+}
+
+// ---- the block's view of its shared memory ---------------------------------
+
+// [3] descriptors, [2][cap + 1] positions, ([2][cap + 1] velocities), then
+// the computing warps' scratch (list build).
+struct BrickSmem {
+  unsigned char *base;
+  int cap;
+  bool vel;
+  __host__ __device__ static size_t desc_bytes() { return 3 * sizeof(BrickDesc); }
+  __host__ __device__ static size_t stage_bytes(int cap, bool vel) {
+    return (size_t)2 * (cap + 1) * sizeof(float4) * (vel ? 2 : 1);
+  }
+  __host__ __device__ static size_t bytes(int cap, bool vel, size_t scratch) {
+    return desc_bytes() + stage_bytes(cap, vel) + scratch;
+  }
+  __device__ __forceinline__ BrickDesc &desc(long long t) const {
+    return reinterpret_cast<BrickDesc *>(base)[t % 3];
+  }
+  __device__ __forceinline__ float4 *pos(long long t) const {
+    return reinterpret_cast<float4 *>(base + desc_bytes()) + (t & 1) * (cap + 1);
+  }
+  __device__ __forceinline__ float4 *vel4(long long t) const {
+    return reinterpret_cast<float4 *>(base + desc_bytes()) + (2 + (t & 1)) * (cap + 1);
+  }
+  __device__ __forceinline__ unsigned char *scratch() const {
+    return base + desc_bytes() + stage_bytes(cap, vel);
+  }
+};
+
+// Copies brick descriptor b from global memory into `dst`, cooperatively
+// (40 16-byte words).
+__device__ __forceinline__ void desc_fetch(const KArgs &a, long long b, BrickDesc &dst) {
+  const uint4 *src = reinterpret_cast<const uint4 *>(a.brick_desc + b);
+  uint4 *d = reinterpret_cast<uint4 *>(&dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(BrickDesc) / 16); k += blockDim.x) d[k] = __ldg(src + k);
+}
+
+// Issues the copies of a brick's stage (positions, and velocities if vel4 is
+// given): warp w takes stage cells w, w + C, ...; its lanes a cell's members.
+__device__ __forceinline__ void stage_issue(const KArgs &a, const BrickDesc &d, float4 *pos,
+                                            float4 *vel4, int cap) {
+  if (d.off[64] > cap) return;  // direct brick
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, C = blockDim.x >> 5;
+  for (int s = warp; s < kStageCells; s += C) {
+    const int o = d.off[s], n = d.off[s + 1] - o, st = d.start[s];
+    for (int m = lane; m < n; m += 32) {
+      cp_async16(pos + 1 + o + m, a.pos4f + st + m);
+      if (vel4) cp_async16(vel4 + 1 + o + m, a.vel4f + st + m);
+    }
+  }
+}
+
+// Adds the stage cells' shifts to their copied offsets (same split as
+// stage_issue); the caller has waited for the copies and synchronised.
+__device__ __forceinline__ void stage_shift_all(const KArgs &a, const BrickDesc &d, float4 *pos,
+                                                int cap) {
+  if (d.off[64] > cap) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, C = blockDim.x >> 5;
+  const Rep &rp = a.rep[d.r];
+  const float hx = rp.hf[0], hy = rp.hf[1], hz = rp.hf[2];  // loaded once, not per cell
+  for (int s = warp; s < kStageCells; s += C) {
+    const int o = d.off[s], n = d.off[s + 1] - o;
+    const float3 h = make_float3(((float)(s & 3) - 1.5f) * hx, ((float)((s >> 2) & 3) - 1.5f) * hy,
+                                 ((float)(s >> 4) - 1.5f) * hz);
+    for (int m = lane; m < n; m += 32) {
+      const float4 v = pos[1 + o + m];
+      pos[1 + o + m] = make_float4(v.x + h.x, v.y + h.y, v.z + h.z, v.w);
+    }
+  }
+}
+
+// Where a staged slot's particle lives: the stage, or (direct bricks) global
+// memory through the descriptor.  Entries are 1 + slot; entry 0 is the
+// far-away sentinel.
+template <bool DIRECT>
+struct StageSrc {
+  const KArgs &a;
+  const BrickDesc &d;
+  const Rep &rp;
+  uint32_t spos, svel;  // shared-window addresses of the stage arrays
+  __device__ __forceinline__ float4 pos(uint32_t e) const {
+    if (!DIRECT) return lds4(spos + e * 16u);
+    if (e == 0u) return make_float4(kFar, kFar, kFar, 0.f);
+    const int s = (int)e - 1, k = stage_cell_of(d, s);
+    float4 v = __ldg(a.pos4f + d.start[k] + (s - d.off[k]));
+    const float3 h = stage_shift(rp, k);
+    v.x += h.x;
+    v.y += h.y;
+    v.z += h.z;
+    return v;
+  }
+  __device__ __forceinline__ float4 vel(uint32_t e) const {
+    if (!DIRECT) return lds4(svel + e * 16u);
+    if (e == 0u) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const int s = (int)e - 1, k = stage_cell_of(d, s);
+    return __ldg(a.vel4f + d.start[k] + (s - d.off[k]));
+  }
+  // cell-list position / particle index of the neighbour in entry e (e > 0)
+  __device__ __forceinline__ int position(uint32_t e) const {
+    const int s = (int)e - 1, k = stage_cell_of(d, s);
+    return d.start[k] + (s - d.off[k]);
+  }
+  __device__ __forceinline__ int32_t index(uint32_t e, bool ident) const {
+    const int p = position(e);
+    return ident ? p : __ldg(a.cell_idx + p);
+  }
+};
+
+// The brick's particle q: its cell-list position, stage cell and staged slot.
+struct HomeSlot {
+  int p, s, slot;
+};
+__device__ __forceinline__ HomeSlot home_slot(const BrickDesc &d, int q) {
+  HomeSlot h;
+  const int i = home_cell_of(d, q);
+  h.p = d.hstart + q;
+  h.s = d.hcell[i];
+  h.slot = h.p + d.hbase[i];
+  return h;
+}
+
+}  // namespace mdgb

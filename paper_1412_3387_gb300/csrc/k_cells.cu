@@ -7,7 +7,7 @@
 // make plain cell lists non-deterministic).  Cells are numbered along a 3-D
 // Hilbert curve per replica, so the cell list's particle order IS the
 // space-filling-curve order used by the sort.
-#include "md_internal.cuh"
+#include "brick.cuh"
 
 namespace mdgb {
 
@@ -17,7 +17,13 @@ __device__ __forceinline__ bool rebuilding(const KArgs &a, int r, int force) {
   return force || a.rebuild[2 * r + (int)(a.ds->step & 1)] != 0;
 }
 
+// Quiet step (no replica rebuilds): every thread leaves at once.
+__device__ __forceinline__ bool quiet(const KArgs &a, int force) {
+  return !force && !a.ds->rebuild_any;
+}
+
 __global__ void k_bin_zero(KArgs a, int force) {
+  if (quiet(a, force)) return;
   int64_t ch = blockIdx.x;
   int r = a.chunk_rep[ch];
   if (!rebuilding(a, r, force)) return;
@@ -26,6 +32,7 @@ __global__ void k_bin_zero(KArgs a, int force) {
 }
 
 __global__ void k_bin_count(KArgs a, int force) {
+  if (quiet(a, force)) return;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   int r = replica_of(a, i);
@@ -79,6 +86,7 @@ __device__ __forceinline__ int block_excl_scan8(int v[8], int *total) {
 }
 
 __global__ void __launch_bounds__(256) k_scan_chunk_sum(KArgs a, int force) {
+  if (quiet(a, force)) return;
   int64_t ch = blockIdx.x;
   int r = a.chunk_rep[ch];
   if (!rebuilding(a, r, force)) return;
@@ -93,6 +101,7 @@ __global__ void __launch_bounds__(256) k_scan_chunk_sum(KArgs a, int force) {
 
 // One warp per replica: exclusive scan of its chunk sums, in place.
 __global__ void k_scan_chunks(KArgs a, int force) {
+  if (quiet(a, force)) return;
   int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
   if (r >= a.R) return;
@@ -115,6 +124,7 @@ __global__ void k_scan_chunks(KArgs a, int force) {
 }
 
 __global__ void __launch_bounds__(256) k_scan_cells(KArgs a, int force) {
+  if (quiet(a, force)) return;
   int64_t ch = blockIdx.x;
   int r = a.chunk_rep[ch];
   if (!rebuilding(a, r, force)) return;
@@ -131,13 +141,17 @@ __global__ void __launch_bounds__(256) k_scan_cells(KArgs a, int force) {
 }
 
 __global__ void k_bin_scatter(KArgs a, int force) {
+  if (quiet(a, force)) return;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   int r = replica_of(a, i);
   if (!rebuilding(a, r, force)) return;
   const Rep &rp = a.rep[r];
   a.cell_idx[a.cell_start[a.pcell[i]] + a.pslot[i]] = (int32_t)i;
-  if (i == rp.p0) a.ident[r] = 0;  // the new binning is not in particle order
+  if (i == rp.p0) {
+    a.ident[r] = 0;    // the new binning is not in particle order
+    a.list_ok[r] = 0;  // and the rows refer to the old one
+  }
   double4 x = ld_d4(a.pos + i);
   int cx = cell_coord(x.x, rp.inv_h[0], rp.nc[0]);
   int cy = cell_coord(x.y, rp.inv_h[1], rp.nc[1]);
@@ -147,32 +161,104 @@ __global__ void k_bin_scatter(KArgs a, int force) {
   o.y = frame_offset_fast(x.y, cy, rp.h[1], rp.half_h[1], rp.L[1]);
   o.z = frame_offset_fast(x.z, cz, rp.h[2], rp.half_h[2], rp.L[2]);
   o.w = __uint_as_float(pack_cell(cx, cy, cz, a.type[i]));
-  a.pos4f[i] = o;
   a.oref[i] = o;
+}
+
+// Particle v goes to cell-list position p: the index maps both ways, and the
+// FP32 copies the staged kernels read (kept in cell-list order) are set.
+__device__ __forceinline__ void place(const KArgs &a, int p, int32_t v) {
+  a.cell_idx[p] = v;
+  a.cellpos[v] = p;
+  a.pos4f[p] = a.oref[v];
+  if (a.vel4f) {
+    const double4 u = ld_d4(a.vel + v);
+    a.vel4f[p] = make_float4((float)u.x, (float)u.y, (float)u.z, __int_as_float(a.tag[v]));
+  }
 }
 
 // One warp per cell: order the cell's members by particle index.
 __global__ void k_cell_sort(KArgs a, int force) {
+  if (quiet(a, force)) return;
   __shared__ int32_t buf[8][kMaxCellSort];
   int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (cell >= a.n_cells) return;
   int r = a.chunk_rep[cell / kChunkCells];
   if (!rebuilding(a, r, force)) return;
-  int cnt = a.cell_count[cell];
-  if (cnt <= 1) return;
+  const int cnt = a.cell_count[cell];
+  if (cnt == 0) return;
+  const int start = a.cell_start[cell];
+  const int32_t *idx = a.cell_idx + start;
   if (cnt > kMaxCellSort) {
+    // flagged; the members keep their binning order
     if (lane == 0) set_error(a.ds, kErrCellOverflow);
+    for (int k = lane; k < cnt; k += 32) place(a, start + k, idx[k]);
     return;
   }
-  int32_t *idx = a.cell_idx + a.cell_start[cell];
   for (int k = lane; k < cnt; k += 32) buf[wid][k] = idx[k];
   __syncwarp();
   for (int k = lane; k < cnt; k += 32) {
     int32_t v = buf[wid][k];
     int rank = 0;
     for (int m = 0; m < cnt; m++) rank += buf[wid][m] < v;
-    idx[rank] = v;
+    place(a, start + rank, v);
+  }
+}
+
+// One warp per brick: the stage layout of its 64 stage cells (first slot and
+// cell-list start of each) and the cell-list range of its own cells.
+__global__ void k_brick_desc(KArgs a, int force) {
+  if (quiet(a, force)) return;
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= a.n_bricks) return;
+  const int4 info = a.brick_info[b];
+  if (!rebuilding(a, info.z, force)) return;
+  BrickDesc &d = a.brick_desc[b];
+  const int32_t c0 = a.brick_stage[b * kStageCells + lane];
+  const int32_t c1 = a.brick_stage[b * kStageCells + 32 + lane];
+  const int n0 = a.cell_count[c0], n1 = a.cell_count[c1];
+  const int st0 = a.cell_start[c0], st1 = a.cell_start[c1];
+  d.start[lane] = st0;
+  d.start[32 + lane] = st1;
+  int i0 = n0, i1 = n1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y0 = __shfl_up_sync(0xffffffffu, i0, o), y1 = __shfl_up_sync(0xffffffffu, i1, o);
+    if (lane >= o) {
+      i0 += y0;
+      i1 += y1;
+    }
+  }
+  const int t0 = __shfl_sync(0xffffffffu, i0, 31);
+  d.off[lane] = i0 - n0;
+  d.off[32 + lane] = t0 + i1 - n1;
+  if (lane == 31) d.off[64] = t0 + i1;
+  // the brick's own cells are the consecutive cell slots info.x, info.x + 1, ...
+  const int nh = __popc(info.y);
+  const int hc = lane < nh ? a.cell_count[info.x + lane] : 0;
+  int hi = hc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, hi, o);
+    if (lane >= o) hi += y;
+  }
+  if (lane < 9) d.hoff[lane] = hi - hc;
+  if (lane == 31) d.nhome = hi;
+  // per own cell: its stage cell and the slot offset of its members
+  const int hs = home_stage_cell(info.y, lane < 8 ? lane : 0);
+  const int src = hs & 31;
+  const int off_lo = __shfl_sync(0xffffffffu, i0 - n0, src);
+  const int off_hi = __shfl_sync(0xffffffffu, t0 + i1 - n1, src);
+  const int st_lo = __shfl_sync(0xffffffffu, st0, src), st_hi = __shfl_sync(0xffffffffu, st1, src);
+  if (lane < 8) {
+    d.hcell[lane] = hs;
+    d.hbase[lane] = hs < 32 ? off_lo - st_lo : off_hi - st_hi;
+  }
+  if (lane == 0) {
+    d.r = info.z;
+    d.hstart = a.cell_start[info.x];
+    d.hmask = info.y;
   }
 }
 
@@ -196,9 +282,7 @@ __global__ void k_sort_gather(KArgs a) {
   a.s_img[k] = a.image[old];
   a.s_tag[k] = a.tag[old];
   a.s_type[k] = a.type[old];
-  a.s_pos4f[k] = a.pos4f[old];
   a.s_oref[k] = a.oref[old];
-  if (a.vel4f) a.s_vel4f[k] = a.vel4f[old];
 }
 
 __global__ void k_sort_scatter(KArgs a) {
@@ -212,11 +296,12 @@ __global__ void k_sort_scatter(KArgs a) {
   int32_t t = a.s_tag[k];
   a.tag[k] = t;
   a.type[k] = a.s_type[k];
-  a.pos4f[k] = a.s_pos4f[k];
   a.oref[k] = a.s_oref[k];
-  if (a.vel4f) a.vel4f[k] = a.s_vel4f[k];
   a.rtag[t] = (int32_t)k;
-  a.cell_idx[k] = (int32_t)k;  // the cell list order is now the particle order
+  // the particle order is now the cell-list order; the FP32 copies, kept in
+  // cell-list order, stay where they are
+  a.cell_idx[k] = (int32_t)k;
+  a.cellpos[k] = (int32_t)k;
   if (k == a.rep[r].p0) a.ident[r] = 1;
 }
 
@@ -233,6 +318,7 @@ cudaError_t launch_bin(const KArgs &a, int force, cudaStream_t st) {
   k_scan_cells<<<(unsigned)a.n_chunks, 256, 0, st>>>(a, force);
   k_bin_scatter<<<blocks_for(a.n, 256), 256, 0, st>>>(a, force);
   k_cell_sort<<<blocks_for(a.n_cells * 32, 256), 256, 0, st>>>(a, force);
+  if (a.n_bricks > 0) k_brick_desc<<<blocks_for(a.n_bricks * 32, 256), 256, 0, st>>>(a, force);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
 // Velocity-Verlet integration with the fused half-buffer rebuild check,
 // harmonic bonds, thermo reductions and small utility kernels.
-#include "md_internal.cuh"
+#include "brick.cuh"
 
 namespace mdgb {
 
@@ -85,20 +85,23 @@ __global__ void k_integrate1(KArgs a) {
     st_d4(a.pos + i, x);
     st_d4(a.vel + i, v);
     if (img.x != img0.x || img.y != img0.y || img.z != img0.z) a.image[i] = img;
-    float4 o = a.pos4f[i];
-    const uint32_t w = __float_as_uint(o.w);
+    // the frame (cell and type in .w) is the one of the last build
+    const float4 ref = a.oref[i];
+    float4 o = ref;
+    const uint32_t w = __float_as_uint(ref.w);
     o.x = frame_offset_fast(x.x, cell_x(w), rp.h[0], rp.half_h[0], rp.L[0]);
     o.y = frame_offset_fast(x.y, cell_y(w), rp.h[1], rp.half_h[1], rp.L[1]);
     o.z = frame_offset_fast(x.z, cell_z(w), rp.h[2], rp.half_h[2], rp.L[2]);
-    a.pos4f[i] = o;
-    const float4 ref = a.oref[i];
+    // the FP32 copies are kept in cell-list order
+    const int64_t p = __ldg(a.ident + r) ? i : (int64_t)a.cellpos[i];
+    a.pos4f[p] = o;
     const float ex = o.x - ref.x, ey = o.y - ref.y, ez = o.z - ref.z;
     const float d2 = ex * ex + ey * ey + ez * ez;
     if (!(d2 <= a.disp2_f)) a.rebuild[2 * r + par] = 1;  // NaN also triggers
     if (!finite_bits(x.x) || !finite_bits(x.y) || !finite_bits(x.z)) {
       if (atomicOr(&a.ds->error, kErrNonfinite) == 0u) a.ds->error_detail = i;
     }
-    if (a.vel4f) a.vel4f[i] = make_float4((float)v.x, (float)v.y, (float)v.z, __int_as_float(a.tag[i]));
+    if (a.vel4f) a.vel4f[p] = make_float4((float)v.x, (float)v.y, (float)v.z, __int_as_float(a.tag[i]));
   }
   // Block barrier, then one fence + ticket per block (release of every
   // thread's flag store through the barrier).
@@ -110,8 +113,10 @@ __global__ void k_integrate1(KArgs a) {
   __syncthreads();
   if (!is_last) return;
   __threadfence();
+  int any = 0;
   for (int r = threadIdx.x; r < a.R; r += blockDim.x) {
     const int rb = __ldcg(a.rebuild + 2 * r + par);
+    any |= rb;
     int now = 0;
     if (a.sort_period > 0 && rb && (t + 1 - __ldcg(a.last_sort + r)) >= a.sort_period) {
       now = 1;
@@ -120,9 +125,10 @@ __global__ void k_integrate1(KArgs a) {
     a.sort_now[r] = now;
     a.rebuild[2 * r + (int)(t & 1)] = 0;
   }
-  __syncthreads();
+  any = __syncthreads_or(any);
   if (threadIdx.x == 0) {
     a.ds->blocks_done = 0u;
+    a.ds->rebuild_any = any;
     a.ds->step = t + 1;
   }
 }
@@ -292,6 +298,7 @@ __global__ void k_init_frames(KArgs a) {
   a.pos4f[i] = o;
   a.oref[i] = o;
   a.cell_idx[i] = (int32_t)i;
+  a.cellpos[i] = (int32_t)i;
   if (ok) a.rtag[tg] = (int32_t)i;
   if (a.vel4f) {
     const double4 v = ld_d4(a.vel + i);
@@ -320,29 +327,25 @@ __global__ void k_export_forces(KArgs a, double *f, double *v) {
   }
 }
 
-// One warp per home cell: decode each row's stage slots into particle indices
-// and write them at the particle's own row.
+// One warp per brick: decode each row's stage slots into particle indices and
+// write them at the particle's own row.
 __global__ void k_export_nlist(KArgs a, int32_t *counts, int32_t *rows) {
-  __shared__ StageInfo si;
   const int lane = threadIdx.x & 31;
-  const int64_t g = blockIdx.x;
-  const int cnt = a.cell_count[g];
-  if (cnt == 0) return;
-  const Rep &rp = a.rep[a.chunk_rep[g / kChunkCells]];
-  stage_info(a, rp, g, si);
-  __syncthreads();
-  const int start = a.cell_start[g];
-  for (int q = 0; q < cnt; q++) {
-    const int p = start + q;
+  const int64_t b = blockIdx.x;
+  const BrickDesc &d = a.brick_desc[b];
+  const int lw = a.w_store_log2, W = 1 << lw, P = 32 >> lw;
+  for (int q = 0; q < d.nhome; q++) {
+    const int p = d.hstart + q;
     const int32_t i = a.cell_idx[p];
     const int nn = a.n_nb[p];
+    const int jg = q / P, q2 = q % P, pj = min(P, d.nhome - jg * P);
+    const uint16_t *grp = a.nl + (size_t)(d.hstart + jg * P) * (size_t)a.max_nb;
     if (lane == 0) counts[i] = nn;
     for (int k = lane; k < a.max_nb; k += 32) {
       int32_t j = -1;
       if (k < nn) {
-        const int slot = a.nl[nl_addr(p, k, a.w_store_log2, a.n_pad)];
-        const int s = stage_cell(si, slot);
-        j = a.cell_idx[si.start[s] + (slot - si.off[s])];
+        const int e = grp[(((k >> lw) * pj + q2) << lw) + (k & (W - 1))];
+        if (e > 0) j = a.cell_idx[d.start[stage_cell_of(d, e - 1)] + (e - 1 - d.off[stage_cell_of(d, e - 1)])];
       }
       rows[(int64_t)i * a.max_nb + k] = j;
     }
@@ -418,7 +421,7 @@ cudaError_t launch_export_forces(const KArgs &a, double *f, double *v, cudaStrea
 
 cudaError_t launch_export_nlist(const KArgs &a, int32_t *counts, int32_t *rows, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  k_export_nlist<<<(unsigned)a.n_cells, 32, 0, st>>>(a, counts, rows);
+  if (a.n_bricks > 0) k_export_nlist<<<(unsigned)a.n_bricks, 32, 0, st>>>(a, counts, rows);
   return cudaGetLastError();
 }
 

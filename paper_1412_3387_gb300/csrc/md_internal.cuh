@@ -26,6 +26,8 @@ enum : uint32_t {
   kErrNonfinite = 1u << 1,
   kErrCellOverflow = 1u << 2,
   kErrBadInput = 1u << 3,
+  kErrTimeout = 1u << 4,
+  kErrStaleList = 1u << 5,  // pair forces asked for before the list of a new binning
 };
 
 // Per-replica constants (device-resident copy + host mirror).
@@ -34,6 +36,8 @@ struct Rep {
   int64_t cell0;      // first cell slot (chunk aligned) in the cell arrays
   int64_t chunk0;     // first scan chunk
   int64_t tchunk0;    // first thermo chunk
+  int64_t brick0;     // first brick (brick.cuh)
+  int64_t nbrick;     // bricks
   int32_t nc[3];      // cells per edge
   int32_t ncell;      // nc0 nc1 nc2
   int32_t nchunk;     // scan chunks
@@ -48,6 +52,8 @@ struct Rep {
   double volume;
 };
 
+struct BrickDesc;  // brick.cuh
+
 // Global device state (one per system, in the workspace).
 struct DevState {
   int64_t step;          // time step of the current positions
@@ -58,7 +64,7 @@ struct DevState {
   int32_t need_max_nb;   // largest row seen when overflowing
   int64_t error_detail;  // particle index of the first non-finite position
   uint32_t blocks_done;  // integrate(1) last-block ticket
-  uint32_t pad0;
+  int32_t rebuild_any;   // some replica's rebuild flag is raised for the current step
   int64_t n_builds;      // replica list builds so far
   int64_t thermo_rows;   // md_run: capacity of thermo_out in rows
 };
@@ -86,20 +92,25 @@ struct KArgs {
   int32_t *tag;
   int32_t *type;
   // internal
-  float4 *pos4f;       // frame-relative FP32 position, packed frame cell + type
-  float4 *oref;        // frame-relative position at the last build
-  float4 *vel4f;       // FP32 velocity, tag bits in w (DPD mixed)
-  int32_t *cell_rank;  // [cells] linear cell -> Hilbert rank (per replica)
-  const uint32_t *stencil;  // [cells][27] neighbour cells by ascending rank | code << 27
+  float4 *pos4f;       // [cell-list position] frame-relative FP32 position, packed frame cell + type
+  float4 *oref;        // [particle] frame-relative position at the last build
+  float4 *vel4f;       // [cell-list position] FP32 velocity, tag bits in w (DPD)
+  int32_t *cellpos;    // [particle] cell-list position
+  int32_t *cell_rank;  // [cells] linear cell -> rank in brick order (per replica)
+  const int32_t *brick_stage;  // [bricks][64] cell slot of each stage cell (brick.cuh)
+  const int4 *brick_info;      // [bricks] first cell slot, cell mask, replica
+  const int32_t *brick_rep;    // [bricks] replica
+  BrickDesc *brick_desc;       // [bricks] stage layouts of the current binning
   int32_t *cell_count; // [cells]
   int32_t *cell_start; // [cells] first particle (global index)
   int32_t *chunk_sum;  // [chunks]
   int32_t *cell_idx;   // [N]
   int32_t *pcell;      // [N] cell slot of each particle (binning)
   int32_t *pslot;      // [N] rank inside its cell (binning)
-  uint16_t *nl;        // [max_nb * n_pad] stage slots, rows indexed by cell position
+  uint16_t *nl;        // [n_pad * max_nb] 1 + stage slot, row groups (pipe.cuh)
+  int32_t *nl_tiles;   // [n_pad] tiles of the row group starting at this cell-list position
   int32_t *n_nb;       // [n_pad] row lengths, indexed by cell position
-  int32_t stage_cap;   // stage slots per warp (pair / list kernels)
+  int32_t stage_cap;   // staged particles per brick buffer
   void *force;         // double4[N] (FP64) or float4[N] (mixed)
   void *virial;        // double[N][6] or float[N][6]
   double *tpart;       // [thermo chunks][8]
@@ -109,15 +120,16 @@ struct KArgs {
   int64_t *last_sort;  // [R]
   int32_t *rtag;       // [N] tag -> index
   int32_t *ident;      // [R] 1 while the replica's particles are in cell order
+  int32_t *list_ok;    // [R] 1 while the replica's list matches its binning
   int32_t *btab;       // [N][max_bonds] partner tags (-1 = none)
   // sort scratch
   double4 *s_pos, *s_vel;
   int4 *s_img;
   int32_t *s_tag, *s_type;
-  float4 *s_pos4f, *s_oref, *s_vel4f;
+  float4 *s_oref;
   const void *coeff;   // LJCoeff* / DPDCoeff* [ntypes^2], precision-matched
   // parameters
-  int32_t max_nb;
+  int32_t max_nb;        // a multiple of 32
   int32_t w_store_log2;  // neighbour-list tile width (pair kernel's w)
   int32_t sort_period;
   int32_t max_bonds;
@@ -130,7 +142,7 @@ struct KArgs {
   double bond_K, bond_r0;
   float disp2_f;       // (r_skin / 2)^2, slightly reduced
   uint64_t seed;
-  int64_t n_chunks, n_tchunks, n_cells;
+  int64_t n_chunks, n_tchunks, n_cells, n_bricks;
 };
 
 // ---- device helpers -------------------------------------------------------
@@ -194,115 +206,6 @@ __device__ __forceinline__ double4 ld_d4(const double4 *p) {
   return make_double4(a.x, a.y, b.x, b.y);
 }
 
-// ---- cell stage ------------------------------------------------------------
-// The stage of home cell g is the concatenation, in ascending Hilbert rank,
-// of the members of the 27 cells around g (g included).  Slot s holds the
-// member's FP32 frame offset plus the offset d h of its cell relative to g
-// (d in {-1,0,1}^3), so that x_i - x_j = o_i - stage[s] for a home particle
-// i.  Rows of the neighbour list hold stage slots (16 bits: a stage has at
-// most 27 x kMaxCellSort slots).  A block stages at most `stage_cap` slots at
-// a time; denser neighbourhoods are processed in windows of that size (rows
-// are in ascending slot order, so each window is a contiguous part of a row).
-struct StageInfo {
-  int off[28];          // first slot of each stencil cell; off[27] = total
-  int start[27];        // cell_start of each stencil cell
-  float sx[27], sy[27], sz[27];  // image shift d h of each stencil cell
-  int self;             // first slot of the home cell's own members
-  int pad[3];
-};
-
-// Filled by the first warp of the block (lanes 0..26: one stencil cell each);
-// the caller synchronises the block before use.
-__device__ __forceinline__ void stage_info(const KArgs &a, const Rep &rp, int64_t g, StageInfo &si) {
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x >= 32) return;
-  int cnt = 0, code = -1;
-  if (lane < 27) {
-    const uint32_t e = __ldg(a.stencil + g * 27 + lane);
-    const int64_t cell = rp.cell0 + (int64_t)(e & kIdxMask);
-    code = (int)(e >> kIdxBits);
-    cnt = __ldg(a.cell_count + cell);
-    si.start[lane] = __ldg(a.cell_start + cell);
-    si.sx[lane] = (float)(code % 3 - 1) * rp.hf[0];
-    si.sy[lane] = (float)((code / 3) % 3 - 1) * rp.hf[1];
-    si.sz[lane] = (float)(code / 9 - 1) * rp.hf[2];
-  }
-  int incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane < 27) si.off[lane] = incl - cnt;
-  if (lane == 26) si.off[27] = incl;
-  if (code == 13) si.self = incl - cnt;
-}
-
-// Stencil cell holding stage slot `slot` (largest s with off[s] <= slot).
-__device__ __forceinline__ int stage_cell(const StageInfo &si, int slot) {
-  int s = 0;
-#pragma unroll
-  for (int step = 16; step >= 1; step >>= 1)
-    if (s + step < 27 && si.off[s + step] <= slot) s += step;
-  return s;
-}
-
-// Fills window slots [w0, w0 + m) of the stage with all threads of the block:
-// positions (pre-shifted), and particle indices / FP32 velocities when idx /
-// vel are given.  Each thread takes slots tid, tid + blockDim, ...; kUnroll of
-// them are looked up and loaded independently before any is stored, so a
-// stage costs about one memory latency.  When the replica's particles are in
-// cell order (`ident`: after each space-filling-curve sort, until the next
-// binning) cell members are index ranges and the cell_idx lookup is skipped.
-// The caller synchronises the block before and after.
-__device__ __forceinline__ void stage_fill(const KArgs &a, const StageInfo &si, int w0, int m,
-                                           bool ident, float4 *pos, int32_t *idx, float4 *vel) {
-  constexpr int kUnroll = 4;
-  const int nt = blockDim.x;
-  for (int b = 0; b < m; b += nt * kUnroll) {
-    int32_t j[kUnroll];
-    int sc[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; u++) {
-      const int k = b + u * nt + threadIdx.x;
-      j[u] = -1;
-      sc[u] = 0;
-      if (k < m) {
-        const int slot = w0 + k;
-        const int s = stage_cell(si, slot);
-        sc[u] = s;
-        const int at = si.start[s] + (slot - si.off[s]);
-        j[u] = ident ? at : __ldg(a.cell_idx + at);
-      }
-    }
-    float4 o[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; u++)
-      o[u] = j[u] >= 0 ? __ldg(a.pos4f + j[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int u = 0; u < kUnroll; u++) {
-      if (j[u] < 0) continue;
-      const int k = b + u * nt + threadIdx.x;
-      const int s = sc[u];
-      pos[k] = make_float4(o[u].x + si.sx[s], o[u].y + si.sy[s], o[u].z + si.sz[s], o[u].w);
-      if (idx) idx[k] = j[u];
-      if (vel) vel[k] = __ldg(a.vel4f + j[u]);
-    }
-  }
-}
-
-// Shared memory of one block: StageInfo, then stage_cap slots of positions,
-// indices and (DPD) velocities.
-__host__ __device__ __forceinline__ size_t stage_bytes(int cap, bool with_vel) {
-  return sizeof(StageInfo) + (size_t)cap * (sizeof(float4) + sizeof(int32_t)) +
-         (with_vel ? (size_t)cap * sizeof(float4) : 0);
-}
-
-// Neighbour-list address of entry k of row p for tile width 2^lw.
-__device__ __forceinline__ size_t nl_addr(int64_t i, int k, int lw, int64_t n_pad) {
-  return ((((size_t)(k >> lw)) * (size_t)n_pad + (size_t)i) << lw) | (size_t)(k & ((1 << lw) - 1));
-}
-
 __device__ __forceinline__ void set_error(DevState *ds, uint32_t bit) { atomicOr(&ds->error, bit); }
 
 // ---- Philox-4x32-10 (Salmon et al., SC'11) --------------------------------
@@ -354,7 +257,9 @@ cudaError_t launch_export_cells(const KArgs &a, int32_t *start, int32_t *count, 
                                 cudaStream_t st);
 cudaError_t launch_philox(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t st);
 cudaError_t launch_init_frames(const KArgs &a, cudaStream_t st);
-int max_block_nlist(int w, int cap);
+int max_block_nlist(const KArgs &a, int w);
 int max_block_pair(const KArgs &a, int w, int want_virial);
+// Blocks of a persistent launch: resident blocks per SM x SMs, at most `work`.
+int persistent_grid(const void *kernel, int threads, size_t smem, int64_t work);
 
 }  // namespace mdgb

@@ -1,0 +1,527 @@
+// Pair forces from the neighbour list (Sec. 5.1: W threads per particle stride
+// over its row; the W partial forces are combined with warp shuffles).
+//
+// Persistent kernel over brick stages (brick.cuh): while a block's warps work
+// on one brick, the next brick's stage (positions relative to the brick
+// centre, plus FP32 velocities for DPD) is copied into shared memory; each
+// warp takes whole row groups of the brick (P = 32 / W particles, W lanes
+// each), so every neighbour position comes from shared memory and every
+// separation is a single FP32 subtraction per component.
+//
+// Potentials: LJ 12-6 (Sec. 3; benchmarks of Sec. 6, 8.3) and DPD in the
+// Groot-Warren form with a Philox-4x32-10 pair noise keyed on the global IDs
+// (Sec. 9: per-pair generators seeded with global particle IDs).
+//
+// Precision forms:
+//   FP64  -- FP64 distance (fixed-order minimum image) and FP64 force math.
+//   mixed -- FP32 separations and force math; each lane sums the forces of a
+//            group of U row entries plainly and adds the group sum to
+//            Kahan-compensated FP32 per-particle sums, which are merged across
+//            the W lanes with error-free two-sums.
+// In both forms the cut-off decision r^2 < r_cut^2 is the FP64 one: an FP32
+// r^2 inside a proven error band around r_cut^2 is re-tested in FP64.
+#pragma once
+
+#include <algorithm>
+
+#include "brick.cuh"
+
+namespace mdgb {
+
+constexpr int kLJ = 0, kDPD = 1;
+
+namespace {
+constexpr unsigned FULL = 0xffffffffu;
+
+// Kahan accumulation: s - c is the running sum.
+struct KSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float y = x - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  // Merge with another lane's (s, c) by an error-free two-sum of the heads.
+  __device__ __forceinline__ void merge(float s2, float c2) {
+    float t = s + s2;
+    float z = t - s;
+    float err = (s - (t - z)) + (s2 - z);
+    c = (c + c2) - err;
+    s = t;
+  }
+  __device__ __forceinline__ float value() const { return s - c; }
+};
+
+template <int W>
+__device__ __forceinline__ void seg_merge(KSum &k) {
+#pragma unroll
+  for (int m = W / 2; m >= 1; m >>= 1) {
+    float s2 = __shfl_xor_sync(FULL, k.s, m);
+    float c2 = __shfl_xor_sync(FULL, k.c, m);
+    k.merge(s2, c2);
+  }
+}
+
+template <int W>
+__device__ __forceinline__ double seg_sum(double v) {
+#pragma unroll
+  for (int m = W / 2; m >= 1; m >>= 1) v += __shfl_xor_sync(FULL, v, m);
+  return v;
+}
+
+// Force on home particle i from the neighbour of entry e (mixed path).  Adds
+// to the group sums (gx, gy, gz) and, with ENERGY, to the energy and virial
+// Kahan sums.  Nothing happens beyond the cut-off.
+template <int POT, bool ENERGY, bool ONE, bool DIRECT>
+struct MixedPair {
+  const KArgs &a;
+  const Rep &rp;
+  const StageSrc<DIRECT> &src;
+  float4 oi, vi4;
+  int ti;
+  bool ident;
+  int32_t i, tag_i;
+  uint64_t step;
+  float rc2_lo, rc2_hi, inv_rc;
+  LJCoeffF lj0;
+  DPDCoeffF dp0;
+  __device__ __forceinline__ void operator()(uint32_t e, float &gx, float &gy, float &gz, KSum &kpe,
+                                             KSum *kw) const {
+    const float4 oj = src.pos(e);
+    const float dx = oi.x - oj.x, dy = oi.y - oj.y, dz = oi.z - oj.z;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    if (!(r2 < rc2_hi)) return;
+    if (r2 >= rc2_lo) {
+      double d[3];
+      if (exact_r2(ld_d4(a.pos + i), ld_d4(a.pos + src.index(e, ident)), rp, d) >= a.rc2) return;
+    }
+    const int cidx = ti * a.ntypes + cell_type(__float_as_uint(oj.w));
+    float fr, v = 0.f;
+    if (POT == kLJ) {
+      const LJCoeffF c = ONE ? lj0 : reinterpret_cast<const LJCoeffF *>(a.coeff)[cidx];
+      const float r2i = __fdividef(1.0f, r2);
+      const float r6 = r2i * r2i * r2i;
+      fr = r2i * r6 * (c.lj1 * r6 - c.lj2);
+      if (ENERGY) v = r6 * (c.lj3 * r6 - c.lj4) - c.vshift;
+    } else {
+      const DPDCoeffF c = ONE ? dp0 : reinterpret_cast<const DPDCoeffF *>(a.coeff)[cidx];
+      const float4 vj = src.vel(e);
+      const float rinv = rsqrtf(r2);
+      const float rr = r2 * rinv;
+      const float w = 1.f - rr * inv_rc;
+      const float dot = dx * (vi4.x - vj.x) + dy * (vi4.y - vj.y) + dz * (vi4.z - vj.z);
+      const uint32_t word = dpd_word(tag_i, __float_as_int(vj.w), step, a.seed);
+      const float uu = ((float)(word >> 8) + 0.5f) * 5.9604644775390625e-08f;  // 2^-24
+      const float theta = 1.7320508075688772f * (2.f * uu - 1.f);
+      const float fmag = c.A * w - c.gamma * w * w * dot * rinv + c.sigma_rdt * w * theta;
+      fr = fmag * rinv;
+      if (ENERGY) v = 0.5f * c.A * (float)a.r_cut * w * w;
+    }
+    const float fx = fr * dx, fy = fr * dy, fz = fr * dz;
+    gx += fx; gy += fy; gz += fz;
+    if (ENERGY) {
+      kpe.add(0.5f * v);
+      kw[0].add(0.5f * dx * fx); kw[1].add(0.5f * dx * fy); kw[2].add(0.5f * dx * fz);
+      kw[3].add(0.5f * dy * fy); kw[4].add(0.5f * dy * fz); kw[5].add(0.5f * dz * fz);
+    }
+  }
+};
+
+// Force on home particle i from the neighbour of entry e (FP64 path).
+template <int POT, bool ENERGY, bool ONE, bool DIRECT>
+struct DoublePair {
+  const KArgs &a;
+  const Rep &rp;
+  const StageSrc<DIRECT> &src;
+  float4 oi;
+  double4 pi, vi;
+  int ti;
+  bool ident;
+  int32_t tag_i;
+  uint64_t step;
+  float rc2_hi;
+  LJCoeffD lj0;
+  DPDCoeffD dp0;
+  __device__ __forceinline__ void operator()(uint32_t e, double *df, double &dpe, double *dw) const {
+    const float4 oj = src.pos(e);
+    const float fx32 = oi.x - oj.x, fy32 = oi.y - oj.y, fz32 = oi.z - oj.z;
+    const float r2f = fmaf(fz32, fz32, fmaf(fy32, fy32, fx32 * fx32));
+    if (!(r2f < rc2_hi)) return;  // FP32 screen: certainly beyond r_cut (or the sentinel)
+    const int32_t j = src.index(e, ident);
+    double d[3];
+    const double r2d = exact_r2(pi, ld_d4(a.pos + j), rp, d);
+    if (r2d >= a.rc2) return;
+    const int cidx = ti * a.ntypes + cell_type(__float_as_uint(oj.w));
+    double fr, v = 0.;
+    if (POT == kLJ) {
+      const LJCoeffD c = ONE ? lj0 : reinterpret_cast<const LJCoeffD *>(a.coeff)[cidx];
+      const double r2i = __drcp_rn(r2d);
+      const double r6 = r2i * r2i * r2i;
+      fr = r2i * r6 * (c.lj1 * r6 - c.lj2);
+      if (ENERGY) v = r6 * (c.lj3 * r6 - c.lj4) - c.vshift;
+    } else {
+      const DPDCoeffD c = ONE ? dp0 : reinterpret_cast<const DPDCoeffD *>(a.coeff)[cidx];
+      const double4 vj = ld_d4(a.vel + j);
+      const double rr = sqrt(r2d);
+      const double rinv = 1.0 / rr;
+      const double w = 1.0 - rr / a.r_cut;
+      const double dot = d[0] * (vi.x - vj.x) + d[1] * (vi.y - vj.y) + d[2] * (vi.z - vj.z);
+      const uint32_t word = dpd_word(tag_i, a.tag[j], step, a.seed);
+      const double uu = ((double)word + 0.5) * 2.3283064365386963e-10;  // 2^-32
+      const double theta = 1.7320508075688772 * (2.0 * uu - 1.0);
+      const double fmag = c.A * w - c.gamma * w * w * dot * rinv + c.sigma_rdt * w * theta;
+      fr = fmag * rinv;
+      if (ENERGY) v = 0.5 * c.A * a.r_cut * w * w;
+    }
+    const double fx = fr * d[0], fy = fr * d[1], fz = fr * d[2];
+    df[0] += fx; df[1] += fy; df[2] += fz;
+    if (ENERGY) {
+      dpe += 0.5 * v;
+      dw[0] += 0.5 * d[0] * fx; dw[1] += 0.5 * d[0] * fy; dw[2] += 0.5 * d[0] * fz;
+      dw[3] += 0.5 * d[1] * fy; dw[4] += 0.5 * d[1] * fz; dw[5] += 0.5 * d[2] * fz;
+    }
+  }
+};
+
+// One row group (P = 32 / W particles of the brick, W lanes each) on one
+// warp.  Rows are read from global memory one block of U tiles ahead.  FULLG:
+// the group has all P particles, so a tile is 32 entries and every row offset
+// is a compile-time constant.
+template <int POT, int W, bool MIXED, bool ENERGY, bool ONE, bool DIRECT, bool FULLG>
+__device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, const float4 *spos,
+                                           const float4 *svel, int j, uint64_t step) {
+  constexpr int P = 32 / W;
+  constexpr int U = 8;
+  const int lane = threadIdx.x & 31;
+  const int qq = lane / W, sl = lane & (W - 1);
+  const int q = j * P + qq;
+  const bool active = q < d.nhome;
+  const int pj = min(P, d.nhome - j * P);
+  const int qe = active ? qq : 0;  // idle lanes shadow the group's first particle
+  const Rep &rp = a.rep[d.r];
+  const bool ident = a.ident[d.r] != 0;
+  const HomeSlot hs = home_slot(d, j * P + qe);
+  const int p = hs.p;
+  const int32_t i = ident ? p : __ldg(a.cell_idx + p);
+  const StageSrc<DIRECT> src{a, d, rp, smem_u32(spos), smem_u32(svel)};
+  const float4 oi = src.pos((uint32_t)(hs.slot + 1));
+  const int pg = d.hstart + j * P;
+  const int T = __ldg(a.nl_tiles + pg);
+  const uint16_t *rows = a.nl + (size_t)pg * (size_t)a.max_nb + qe * W + sl;
+  const int stride = FULLG ? 32 : pj * W;  // entries per tile
+
+  KSum kf[3], kpe, kw[6];
+  double df[3] = {0., 0., 0.}, dpe = 0., dw[6] = {0., 0., 0., 0., 0., 0.};
+  MixedPair<POT, ENERGY, ONE, DIRECT> mp{a, rp, src};
+  DoublePair<POT, ENERGY, ONE, DIRECT> dp{a, rp, src};
+  if (MIXED) {
+    mp.oi = oi;
+    mp.ti = cell_type(__float_as_uint(oi.w));
+    mp.ident = ident;
+    mp.i = i;
+    mp.step = step;
+    mp.rc2_lo = a.rc2f - rp.band;
+    mp.rc2_hi = a.rc2f + rp.band;
+    mp.inv_rc = (float)(1.0 / a.r_cut);
+    if (ONE) {
+      if (POT == kLJ) mp.lj0 = reinterpret_cast<const LJCoeffF *>(a.coeff)[0];
+      else mp.dp0 = reinterpret_cast<const DPDCoeffF *>(a.coeff)[0];
+    }
+    if (POT == kDPD) {
+      mp.vi4 = src.vel((uint32_t)(hs.slot + 1));
+      mp.tag_i = __float_as_int(mp.vi4.w);
+    }
+  } else {
+    dp.oi = oi;
+    dp.ti = cell_type(__float_as_uint(oi.w));
+    dp.ident = ident;
+    dp.pi = ld_d4(a.pos + i);
+    dp.step = step;
+    dp.rc2_hi = a.rc2f + rp.band;
+    if (ONE) {
+      if (POT == kLJ) dp.lj0 = reinterpret_cast<const LJCoeffD *>(a.coeff)[0];
+      else dp.dp0 = reinterpret_cast<const DPDCoeffD *>(a.coeff)[0];
+    }
+    if (POT == kDPD) {
+      dp.vi = ld_d4(a.vel + i);
+      dp.tag_i = a.tag[i];
+    }
+  }
+
+  // U entries at a time; the full blocks load the next block ahead without
+  // bounds tests, the last T mod U tiles go one at a time (nu = 1)
+  auto work = [&](const uint32_t *e, const int nu) {
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (MIXED && POT == kLJ) {
+      // straight-line LJ: every entry is evaluated and masked (the sentinel's
+      // r^2 is +inf); entries in the FP64 tie-break band are settled after
+      // the group
+      bool band = false;
+#pragma unroll
+      for (int u = 0; u < nu; u++) {
+        const float4 oj = src.pos(e[u]);
+        const float dx = oi.x - oj.x, dy = oi.y - oj.y, dz = oi.z - oj.z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const bool in = r2 < mp.rc2_lo;
+        band |= (r2 >= mp.rc2_lo) & (r2 < mp.rc2_hi);
+        const LJCoeffF c = ONE ? mp.lj0
+                               : reinterpret_cast<const LJCoeffF *>(a.coeff)[
+                                     mp.ti * a.ntypes + cell_type(__float_as_uint(oj.w))];
+        const float r2i = __fdividef(1.0f, r2);
+        const float r6 = r2i * r2i * r2i;
+        const float fr = in ? r2i * r6 * (c.lj1 * r6 - c.lj2) : 0.f;
+        gx = fmaf(fr, dx, gx);
+        gy = fmaf(fr, dy, gy);
+        gz = fmaf(fr, dz, gz);
+        if (ENERGY) {
+          const float v = in ? r6 * (c.lj3 * r6 - c.lj4) - c.vshift : 0.f;
+          const float fx = fr * dx, fy = fr * dy, fz = fr * dz;
+          kpe.add(0.5f * v);
+          kw[0].add(0.5f * dx * fx); kw[1].add(0.5f * dx * fy); kw[2].add(0.5f * dx * fz);
+          kw[3].add(0.5f * dy * fy); kw[4].add(0.5f * dy * fz); kw[5].add(0.5f * dz * fz);
+        }
+      }
+      if (__any_sync(FULL, band)) {
+#pragma unroll
+        for (int u = 0; u < nu; u++) {
+          const float4 oj = src.pos(e[u]);
+          const float dx = oi.x - oj.x, dy = oi.y - oj.y, dz = oi.z - oj.z;
+          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          if (r2 >= mp.rc2_lo && r2 < mp.rc2_hi) mp(e[u], gx, gy, gz, kpe, kw);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < nu; u++) {
+        if (e[u] == 0u) continue;  // padding
+        if (MIXED) mp(e[u], gx, gy, gz, kpe, kw);
+        else dp(e[u], df, dpe, dw);
+      }
+    }
+    if (MIXED) {
+      kf[0].add(gx);
+      kf[1].add(gy);
+      kf[2].add(gz);
+    }
+  };
+  const int Tm = T & ~(U - 1);
+  uint32_t nxt[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) nxt[u] = u < T ? (uint32_t)__ldcs(rows + u * stride) : 0u;
+  for (int t0 = 0; t0 < Tm; t0 += U) {
+    uint32_t e[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) e[u] = nxt[u];
+    const uint16_t *r = rows + (size_t)(t0 + U) * stride;
+    if (t0 + 2 * U <= T) {
+#pragma unroll
+      for (int u = 0; u < U; u++) nxt[u] = (uint32_t)__ldcs(r + u * stride);
+    } else {
+      // the tail tiles come in with the last full block
+#pragma unroll
+      for (int u = 0; u < U; u++) nxt[u] = t0 + U + u < T ? (uint32_t)__ldcs(r + u * stride) : 0u;
+    }
+    work(e, U);
+  }
+  // the last T mod U tiles, already loaded, one at a time
+  const int rem = T - Tm;
+#pragma unroll
+  for (int u = 0; u < U; u++)
+    if (u < rem) work(&nxt[u], 1);
+
+  // combine the W partial sums of each particle (intra-warp reduction)
+  if (MIXED) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) seg_merge<W>(kf[c]);
+    if (ENERGY) {
+      seg_merge<W>(kpe);
+#pragma unroll
+      for (int c = 0; c < 6; c++) seg_merge<W>(kw[c]);
+    }
+    if (active && sl == 0) {
+      float4 *f = reinterpret_cast<float4 *>(a.force);
+      f[i] = make_float4(kf[0].value(), kf[1].value(), kf[2].value(), ENERGY ? kpe.value() : 0.f);
+      if (ENERGY) {
+        float *vv = reinterpret_cast<float *>(a.virial) + 6 * (int64_t)i;
+#pragma unroll
+        for (int c = 0; c < 6; c++) vv[c] = kw[c].value();
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; c++) df[c] = seg_sum<W>(df[c]);
+    if (ENERGY) {
+      dpe = seg_sum<W>(dpe);
+#pragma unroll
+      for (int c = 0; c < 6; c++) dw[c] = seg_sum<W>(dw[c]);
+    }
+    if (active && sl == 0) {
+      double2 *f = reinterpret_cast<double2 *>(reinterpret_cast<double4 *>(a.force) + i);
+      f[0] = make_double2(df[0], df[1]);
+      f[1] = make_double2(df[2], ENERGY ? dpe : 0.);
+      if (ENERGY) {
+        double *vv = reinterpret_cast<double *>(a.virial) + 6 * (int64_t)i;
+#pragma unroll
+        for (int c = 0; c < 6; c++) vv[c] = dw[c];
+      }
+    }
+  }
+}
+
+// Persistent over bricks b = blockIdx + t G.  Warp w takes the brick's row
+// groups w, w + C, ...; the next brick's stage copies run meanwhile.
+template <int POT, int W, bool MIXED, bool ENERGY, bool ONE>
+__global__ void __launch_bounds__(kMaxBrickThreads) k_pair(KArgs a, int cap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int P = 32 / W;
+  constexpr bool VEL = POT == kDPD && MIXED;
+  const BrickSmem M{smem, cap, VEL};
+  const int warp = threadIdx.x >> 5, C = blockDim.x >> 5;
+  const long long G = gridDim.x, b0 = blockIdx.x;
+  const uint64_t step = (uint64_t)a.ds->step;
+  if (b0 >= a.n_bricks) return;
+  if (threadIdx.x < 2) {
+    M.pos(threadIdx.x)[0] = make_float4(kFar, kFar, kFar, 0.f);
+    if (VEL) M.vel4(threadIdx.x)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  desc_fetch(a, b0, M.desc(0));
+  if (b0 + G < a.n_bricks) desc_fetch(a, b0 + G, M.desc(1));
+  __syncthreads();
+  stage_issue(a, M.desc(0), M.pos(0), VEL ? M.vel4(0) : nullptr, cap);
+  cp_async_wait_all();
+  __syncthreads();
+  stage_shift_all(a, M.desc(0), M.pos(0), cap);
+  __syncthreads();
+  constexpr int kDescWords = (int)(sizeof(BrickDesc) / 16);
+  for (long long t = 0;; t++) {
+    const long long bt = b0 + t * G;
+    if (bt >= a.n_bricks) break;
+    const bool has1 = bt + G < a.n_bricks, has2 = bt + 2 * G < a.n_bricks;
+    if (has1) stage_issue(a, M.desc(t + 1), M.pos(t + 1), VEL ? M.vel4(t + 1) : nullptr, cap);
+    // the descriptor two bricks ahead: loaded now, stored after the work
+    // (40 words; a block has at least 32 threads, so two per thread)
+    uint4 dv0 = make_uint4(0u, 0u, 0u, 0u), dv1 = dv0;
+    const int k0 = threadIdx.x, k1 = threadIdx.x + blockDim.x;
+    if (has2) {
+      const uint4 *src = reinterpret_cast<const uint4 *>(a.brick_desc + bt + 2 * G);
+      if (k0 < kDescWords) dv0 = __ldg(src + k0);
+      if (k1 < kDescWords) dv1 = __ldg(src + k1);
+    }
+    const BrickDesc &d = M.desc(t);
+    const int ng = (d.nhome + P - 1) / P;
+    if (d.off[64] > cap) {
+      for (int j = warp; j < ng; j += C)
+        pair_group<POT, W, MIXED, ENERGY, ONE, true, false>(a, d, M.pos(t), M.vel4(t), j, step);
+    } else {
+      for (int j = warp; j < ng; j += C) {
+        if ((j + 1) * P <= d.nhome)
+          pair_group<POT, W, MIXED, ENERGY, ONE, false, true>(a, d, M.pos(t), M.vel4(t), j, step);
+        else
+          pair_group<POT, W, MIXED, ENERGY, ONE, false, false>(a, d, M.pos(t), M.vel4(t), j, step);
+      }
+    }
+    if (has2) {
+      uint4 *dst = reinterpret_cast<uint4 *>(&M.desc(t + 2));
+      if (k0 < kDescWords) dst[k0] = dv0;
+      if (k1 < kDescWords) dst[k1] = dv1;
+    }
+    cp_async_wait_all();
+    __syncthreads();  // brick t done everywhere; brick t + 1's copies have landed
+    if (has1) stage_shift_all(a, M.desc(t + 1), M.pos(t + 1), cap);
+    __syncthreads();
+  }
+}
+
+template <int POT, int W, bool MIXED, bool ENERGY, bool ONE>
+cudaError_t go1(const KArgs &a, int block, cudaStream_t st) {
+  constexpr bool VEL = POT == kDPD && MIXED;
+  const size_t smem = BrickSmem::bytes(a.stage_cap, VEL, 0);
+  const auto kern = k_pair<POT, W, MIXED, ENERGY, ONE>;
+  const int grid = persistent_grid((const void *)kern, block, smem, a.n_bricks);
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  kern<<<grid, block, smem, st>>>(a, a.stage_cap);
+  return cudaGetLastError();
+}
+
+template <int POT, int W, bool MIXED, bool ENERGY>
+cudaError_t go(const KArgs &a, int block, cudaStream_t st) {
+  if (a.ntypes == 1) return go1<POT, W, MIXED, ENERGY, true>(a, block, st);
+  return go1<POT, W, MIXED, ENERGY, false>(a, block, st);
+}
+
+template <int POT, bool MIXED, bool ENERGY>
+cudaError_t go_w(const KArgs &a, Launch l, cudaStream_t st) {
+  switch (l.w) {
+    case 1: return go<POT, 1, MIXED, ENERGY>(a, l.block, st);
+    case 2: return go<POT, 2, MIXED, ENERGY>(a, l.block, st);
+    case 4: return go<POT, 4, MIXED, ENERGY>(a, l.block, st);
+    case 8: return go<POT, 8, MIXED, ENERGY>(a, l.block, st);
+    case 16: return go<POT, 16, MIXED, ENERGY>(a, l.block, st);
+    case 32: return go<POT, 32, MIXED, ENERGY>(a, l.block, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int POT, int W, bool MIXED, bool ENERGY>
+int maxb_w() {
+  cudaFuncAttributes a1, a2;
+  if (cudaFuncGetAttributes(&a1, k_pair<POT, W, MIXED, ENERGY, true>) != cudaSuccess) return 0;
+  if (cudaFuncGetAttributes(&a2, k_pair<POT, W, MIXED, ENERGY, false>) != cudaSuccess) return 0;
+  return std::min(a1.maxThreadsPerBlock, a2.maxThreadsPerBlock);
+}
+
+template <int POT, bool MIXED, bool ENERGY>
+int maxb(int w) {
+  switch (w) {
+    case 1: return maxb_w<POT, 1, MIXED, ENERGY>();
+    case 2: return maxb_w<POT, 2, MIXED, ENERGY>();
+    case 4: return maxb_w<POT, 4, MIXED, ENERGY>();
+    case 8: return maxb_w<POT, 8, MIXED, ENERGY>();
+    case 16: return maxb_w<POT, 16, MIXED, ENERGY>();
+    case 32: return maxb_w<POT, 32, MIXED, ENERGY>();
+  }
+  return 0;
+}
+
+template <int POT, int W, bool MIXED, bool ENERGY>
+void allow_w() {
+  cudaFuncSetAttribute(k_pair<POT, W, MIXED, ENERGY, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(k_pair<POT, W, MIXED, ENERGY, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+template <int POT, bool MIXED, bool ENERGY>
+void allow_all_w() {
+  allow_w<POT, 1, MIXED, ENERGY>(); allow_w<POT, 2, MIXED, ENERGY>();
+  allow_w<POT, 4, MIXED, ENERGY>(); allow_w<POT, 8, MIXED, ENERGY>();
+  allow_w<POT, 16, MIXED, ENERGY>(); allow_w<POT, 32, MIXED, ENERGY>();
+}
+
+}  // namespace
+
+// Entry points of one (potential, precision) form; each form is compiled in
+// its own translation unit (k_pair_<form>.cu) to keep builds parallel.
+template <int POT, bool MIXED>
+cudaError_t launch_pair_form(const KArgs &a, Launch l, int want_virial, cudaStream_t st) {
+  return want_virial ? go_w<POT, MIXED, true>(a, l, st) : go_w<POT, MIXED, false>(a, l, st);
+}
+
+template <int POT, bool MIXED>
+int max_block_pair_form(int w, int want_virial) {
+  return want_virial ? maxb<POT, MIXED, true>(w) : maxb<POT, MIXED, false>(w);
+}
+
+template <int POT, bool MIXED>
+void pair_form_attributes() {
+  allow_all_w<POT, MIXED, false>();
+  allow_all_w<POT, MIXED, true>();
+}
+
+#define MDGB_PAIR_FORM(POT, MIXED)                                                         \
+  template cudaError_t launch_pair_form<POT, MIXED>(const KArgs &, Launch, int, cudaStream_t); \
+  template int max_block_pair_form<POT, MIXED>(int, int);                                  \
+  template void pair_form_attributes<POT, MIXED>();
+
+}  // namespace mdgb

@@ -20,7 +20,7 @@ MD_OK = 0
 STATUS = {
     0: "MD_OK", 1: "MD_ERR_INVALID_ARG", 2: "MD_ERR_CUDA", 3: "MD_ERR_WORKSPACE_TOO_SMALL",
     4: "MD_ERR_NLIST_OVERFLOW", 5: "MD_ERR_CELL_GRID", 6: "MD_ERR_NONFINITE",
-    7: "MD_ERR_CELL_OVERFLOW", 8: "MD_ERR_STATE",
+    7: "MD_ERR_CELL_OVERFLOW", 8: "MD_ERR_STATE", 9: "MD_ERR_TIMEOUT",
 }
 FP64, MIXED = 0, 1
 LJ, DPD = 0, 1

@@ -159,6 +159,25 @@ def test_lj_fp64_forces_match_oracle(w):
     assert np.allclose(v, vref, rtol=1e-11, atol=1e-12 * absf.max())
 
 
+@pytest.mark.parametrize("w", (1, 2))
+def test_smallest_blocks_lists_and_forces(w):
+    # one warp per block: the per-brick descriptor is copied two words per thread
+    st = lj_state(n=3001, jitter=0.1)
+    L = st.box[0]
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005)
+    s.set_tuning(md.KERNEL_PAIR, 32, w)
+    s.set_tuning(md.KERNEL_NLIST, 32, w)
+    s.prepare()
+    counts, rows = (x.cpu().numpy() for x in s.nlist())
+    cb, rb = oracle.neighbors(st.pos, L, 2.8, max_nb=s.max_nb, method="brute")
+    assert np.array_equal(counts, cb)
+    for i in range(st.n):
+        assert np.array_equal(np.sort(rows[i, :counts[i]]), rb[i, :cb[i]]), i
+    ref, _, absf = oracle.lj_forces(st.pos, L, 2.5)
+    fp64_force_check(s.forces().cpu().numpy(), ref, absf, f"w={w}")
+    s.check_error()
+
+
 def test_lj_fp64_shifted_energy_and_multitype():
     st = lj_state(n=2999, jitter=0.1)
     t = (np.arange(st.n) * 7919 % 3).astype(np.int32)
@@ -251,6 +270,58 @@ def test_fp64_trajectory_matches_oracle_100_steps():
     assert np.max(np.abs(g["vel"][:, :3] - out["vel"][:, :3])) < 1e-8
     assert np.allclose(th, out["thermo"], rtol=1e-9, atol=1e-9)
     assert s.get_step() == 100
+
+
+def test_fp64_trajectory_sorted_every_rebuild():
+    # sort_period = 1: the particles are reordered along the cell curve at every
+    # rebuild, so the staged kernels take the in-order path; compare by tag
+    st = lj_state(n=4000, T=1.44, jitter=0.05)
+    L = st.box[0]
+    out = oracle.run(st.pos, st.vel, st.image, L, 100, r_cut=2.5, r_skin=0.3, dt=0.005)
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, sort_period=1)
+    s.run(100)
+    s.check_error()
+    g = s.state_numpy()
+    by_tag = np.argsort(g["tag"])
+    x0 = out["pos"][:, :3] + out["image"][:, :3] * L
+    x1 = (g["pos"][:, :3] + g["image"][:, :3] * L)[by_tag]
+    assert not np.array_equal(g["tag"], np.arange(st.n))  # it did sort
+    assert np.max(np.abs(x1 - x0)) < 1e-9
+    assert np.max(np.abs(g["vel"][by_tag, :3] - out["vel"][:, :3])) < 1e-8
+
+
+def half_empty_box(n=4000, seed=23):
+    """A fluid at density 0.8442 in one corner sub-cube of a box of twice its
+    volume: its cells hold about twice the box's mean occupancy, beyond the
+    kernels' shared-memory buffers, so those cells are served from global
+    memory."""
+    st = lj_state(n=n, seed=seed, jitter=0.1)
+    st.box = st.box * 2.0 ** (1.0 / 3.0)
+    return st
+
+
+@pytest.mark.parametrize("w", (1, 4))
+def test_overfull_cells_lists_and_forces(w):
+    st = half_empty_box()
+    L = st.box[0]
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005)
+    s.set_tuning(md.KERNEL_PAIR, 128, w)
+    s.set_tuning(md.KERNEL_NLIST, 64, w)
+    s.prepare()
+    counts, rows = (x.cpu().numpy() for x in s.nlist())
+    cb, rb = oracle.neighbors(st.pos, L, 2.8, max_nb=s.max_nb, method="brute")
+    assert np.array_equal(counts, cb)
+    for i in range(st.n):
+        assert np.array_equal(np.sort(rows[i, :counts[i]]), rb[i, :cb[i]]), i
+    ref, _, absf = oracle.lj_forces(st.pos, L, 2.5)
+    fp64_force_check(s.forces().cpu().numpy(), ref, absf, f"w={w}")
+    m = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, precision="mixed")
+    m.set_tuning(md.KERNEL_PAIR, 128, w)
+    m.prepare()
+    rms, mx = mixed_force_stats(m.forces().cpu().numpy(), ref, absf)
+    assert rms <= 1e-5 and mx <= 1e-3, (rms, mx)
+    s.check_error()
+    m.check_error()
 
 
 def test_thermo_matches_oracle_and_is_reproducible():

@@ -382,9 +382,9 @@ def test_hilbert_is_a_unit_step_bijection(bits):
     assert idx[0] == (0, 0, 0)
 
 
-def test_sfc_order_is_permutation_walking_adjacent_cells():
-    L = 12.0
-    nc = 4  # r_list 3.0 -> 4 cells of width 3
+def test_sfc_order_is_permutation_walking_adjacent_bricks():
+    L = 24.0
+    nc = 8  # r_list 3.0 -> 8 cells of width 3, 4 bricks of 2 x 2 x 2 cells per edge
     cells = np.array([(x, y, z) for x in range(nc) for y in range(nc) for z in range(nc)])
     rng = np.random.default_rng(2)
     perm = rng.permutation(len(cells))
@@ -393,4 +393,13 @@ def test_sfc_order_is_permutation_walking_adjacent_cells():
     order = oracle.sfc_order(pos, L, 3.0)
     assert sorted(order.tolist()) == list(range(len(cells)))
     walk = cells[perm][order]
-    assert np.all(np.abs(np.diff(walk, axis=0)).sum(1) == 1)
+    bricks = walk // 2
+    # each run of 8 is one brick, its cells x first, then y, then z
+    for k in range(0, len(walk), 8):
+        assert np.all(bricks[k:k + 8] == bricks[k])
+        local = walk[k:k + 8] % 2
+        assert (local[:, 0] + 2 * local[:, 1] + 4 * local[:, 2]).tolist() == list(range(8))
+    # and the bricks follow the Hilbert curve: unit steps, starting at the origin
+    b = bricks[::8]
+    assert np.all(np.abs(np.diff(b, axis=0)).sum(1) == 1)
+    assert b[0].tolist() == [0, 0, 0]
