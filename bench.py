@@ -208,16 +208,25 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+PAIR_SOURCES = ("pair_impl.cuh", "brick.cuh", "md_internal.cuh")
+
+
+def pair_source_hash():
+    h = hashlib.sha256()
+    for name in PAIR_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1412_3387_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def pair_traffic_record():
-    """DRAM bytes per pair-kernel launch from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
+    """DRAM bytes per pair-kernel launch (scaled to this workload) from the
+    committed ncu summary, if it was taken on the current kernel sources;
+    else None."""
     path = os.path.join(ROOT, "profiles", "pair_lj_mixed_traffic.json")
-    src = os.path.join(ROOT, "paper_1412_3387_gb300", "csrc", "k_pair.cu")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("k_pair_sha256_16") != h:
+    if rec.get("pair_sources_sha256_16") != pair_source_hash():
         return None
     return rec
 
@@ -316,8 +325,11 @@ def main():
         else:
             peak, peak_src = 6800.0, "fallback"
         rec = pair_traffic_record()
+        traffic = None
+        if rec:  # scaled by the particles of one launch
+            traffic = rec["dram_bytes_per_particle"] * args.n
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": rec["dram_bytes_per_launch"] if rec else None,
+                    "frac": achieved / peak, "traffic": traffic,
                     "kernel": "k_pair<LJ, mixed>", "peak_source": peak_src,
                     "ms_per_launch": pair_ms, "algorithmic_bytes_per_particle": bytes_per_particle,
                     "mean_neighbours": nbar}
@@ -347,9 +359,11 @@ def main():
         del sysm
         torch.cuda.empty_cache()
 
-        # launches in the timed region: per step integrate(1) + 7 binning +
-        # 2 sort + nlist + pair + integrate(2); 2 thermo kernels per thermo step
-        launches = args.steps * (1 + 7 + 2 + 1 + 1 + 1) + 2 * (args.steps // 100)
+        # launches in the timed region: per step integrate(1) + 8 binning
+        # (7 cell-list kernels + brick descriptors) + 2 sort + nlist + pair +
+        # integrate(2); 2 thermo kernels per thermo step.  The binning, sort
+        # and list kernels return at once on steps without a rebuild.
+        launches = args.steps * (1 + 8 + 2 + 1 + 1 + 1) + 2 * (args.steps // 100)
 
         forms = {"mixed": {"value": value, "ms_per_step": ms_per_step, "steps": args.steps}}
         if args.forms == "all":
