@@ -83,9 +83,9 @@ struct Plan {
   int64_t n = 0, n_pad = 0, n_cells = 0, n_chunks = 0, n_tchunks = 0;
   int32_t max_nb = 0;
   int32_t stage_cap = 0;
-  int64_t n_bricks = 0;
+  int64_t n_bricks = 0, n_ctab = 0;
   // byte offsets into the workspace
-  size_t o_rep, o_off, o_chunk_rep, o_tchunk_rep, o_cell_rank, o_brick_stage, o_brick_info,
+  size_t o_rep, o_off, o_chunk_rep, o_tchunk_rep, o_cell_rank, o_ctab, o_brick_stage, o_brick_info,
       o_brick_rep, o_brick_desc, o_cell_count, o_cell_start,
       o_chunk_sum, o_cell_idx, o_cellpos, o_pcell, o_pslot, o_n_nb, o_rtag, o_pos4f, o_oref, o_vel4f,
       o_nl, o_nl_tiles, o_force, o_virial, o_tpart, o_ds, o_rebuild, o_sort_now, o_last_sort, o_ident,
@@ -147,6 +147,7 @@ md_status make_plan(const md_params *p, Plan &pl) {
       rp.half_h[d] = 0.5 * rp.h[d];
       rp.inv_h[d] = (double)rp.nc[d] / L;
       rp.hf[d] = (float)rp.h[d];
+      rp.Lf[d] = (float)L;
       hmax = std::max(hmax, rp.h[d]);
     }
     // FP32 r^2 error bound: |o| <= (h + skin) / 2 per coordinate; each
@@ -162,6 +163,8 @@ md_status make_plan(const md_params *p, Plan &pl) {
     rp.chunk0 = chunk0;
     rp.tchunk0 = tchunk0;
     rp.brick0 = pl.n_bricks;
+    rp.ctab0 = pl.n_ctab;
+    pl.n_ctab += rp.nc[0] + rp.nc[1] + rp.nc[2];
     rp.nbrick = ((rp.nc[0] + 1) / 2) * ((rp.nc[1] + 1) / 2) * ((rp.nc[2] + 1) / 2);
     pl.n_bricks += rp.nbrick;
     cell0 += (int64_t)rp.nchunk * kChunkCells;
@@ -194,6 +197,7 @@ md_status make_plan(const md_params *p, Plan &pl) {
   pl.o_chunk_rep = take(sizeof(int32_t) * pl.n_chunks);
   pl.o_tchunk_rep = take(sizeof(int32_t) * pl.n_tchunks);
   pl.o_cell_rank = take(sizeof(int32_t) * pl.n_cells);
+  pl.o_ctab = take(sizeof(double) * (size_t)pl.n_ctab);
   pl.o_brick_stage = take(sizeof(int32_t) * kStageCells * (size_t)pl.n_bricks);
   pl.o_brick_info = take(sizeof(int4) * (size_t)pl.n_bricks);
   pl.o_brick_rep = take(sizeof(int32_t) * (size_t)pl.n_bricks);
@@ -378,6 +382,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   a.oref = at<float4>(ws, pl.o_oref);
   a.vel4f = dpd ? at<float4>(ws, pl.o_vel4f) : nullptr;
   a.cell_rank = at<int32_t>(ws, pl.o_cell_rank);
+  a.ctab = at<double>(ws, pl.o_ctab);
   a.brick_stage = at<int32_t>(ws, pl.o_brick_stage);
   a.brick_info = at<int4>(ws, pl.o_brick_info);
   a.brick_rep = at<int32_t>(ws, pl.o_brick_rep);
@@ -441,10 +446,13 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   std::vector<int32_t> bstage((size_t)pl.n_bricks * kStageCells, 0);
   std::vector<int4> binfo((size_t)pl.n_bricks);
   std::vector<int32_t> brep((size_t)pl.n_bricks, 0);
+  std::vector<double> ctab((size_t)pl.n_ctab, 0.0);
   for (int r = 0; r < R; r++) {
     const Rep &rp = pl.reps[r];
     for (int c = 0; c < rp.nchunk; c++) chunk_rep[rp.chunk0 + c] = r;
     for (int c = 0; c < rp.ntchunk; c++) tchunk_rep[rp.tchunk0 + c] = r;
+    for (int d = 0, off = 0; d < 3; off += rp.nc[d], d++)
+      for (int c = 0; c < rp.nc[d]; c++) ctab[rp.ctab0 + off + c] = std::fma((double)c, rp.h[d], rp.half_h[d]);
     const int nb[3] = {(rp.nc[0] + 1) / 2, (rp.nc[1] + 1) / 2, (rp.nc[2] + 1) / 2};
     const int nmax = std::max(nb[0], std::max(nb[1], nb[2]));
     int bits = 1;
@@ -526,6 +534,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
       cudaMemcpyAsync(at<void>(ws, pl.o_chunk_rep), chunk_rep.data(), sizeof(int32_t) * pl.n_chunks, cudaMemcpyHostToDevice, stream) ||
       cudaMemcpyAsync(at<void>(ws, pl.o_tchunk_rep), tchunk_rep.data(), sizeof(int32_t) * pl.n_tchunks, cudaMemcpyHostToDevice, stream) ||
       cudaMemcpyAsync(at<void>(ws, pl.o_cell_rank), rank.data(), sizeof(int32_t) * pl.n_cells, cudaMemcpyHostToDevice, stream) ||
+      cudaMemcpyAsync(at<void>(ws, pl.o_ctab), ctab.data(), sizeof(double) * ctab.size(), cudaMemcpyHostToDevice, stream) ||
       cudaMemcpyAsync(at<void>(ws, pl.o_brick_stage), bstage.data(), sizeof(int32_t) * bstage.size(), cudaMemcpyHostToDevice, stream) ||
       cudaMemcpyAsync(at<void>(ws, pl.o_brick_info), binfo.data(), sizeof(int4) * binfo.size(), cudaMemcpyHostToDevice, stream) ||
       cudaMemcpyAsync(at<void>(ws, pl.o_brick_rep), brep.data(), sizeof(int32_t) * brep.size(), cudaMemcpyHostToDevice, stream) ||

@@ -31,10 +31,7 @@ __global__ void k_bin_zero(KArgs a, int force) {
   for (int k = threadIdx.x; k < kChunkCells; k += blockDim.x) cnt[k] = 0;
 }
 
-__global__ void k_bin_count(KArgs a, int force) {
-  if (quiet(a, force)) return;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+__device__ __forceinline__ void k_bin_count_one(const KArgs &a, int64_t i, int force) {
   int r = replica_of(a, i);
   if (!rebuilding(a, r, force)) return;
   const Rep &rp = a.rep[r];
@@ -46,6 +43,13 @@ __global__ void k_bin_count(KArgs a, int force) {
   int64_t g = rp.cell0 + a.cell_rank[rp.cell0 + lin];
   a.pcell[i] = (int32_t)g;
   a.pslot[i] = atomicAdd(a.cell_count + g, 1);
+}
+
+__global__ void k_bin_count(KArgs a, int force) {
+  if (quiet(a, force)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    k_bin_count_one(a, i, force);
 }
 
 // Block-wide exclusive scan of 8 values per thread (256 threads).
@@ -140,10 +144,7 @@ __global__ void __launch_bounds__(256) k_scan_cells(KArgs a, int force) {
   for (int k = 0; k < 8; k++) a.cell_start[c0 + k] = off + v[k];
 }
 
-__global__ void k_bin_scatter(KArgs a, int force) {
-  if (quiet(a, force)) return;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
+__device__ __forceinline__ void k_bin_scatter_one(const KArgs &a, int64_t i, int force) {
   int r = replica_of(a, i);
   if (!rebuilding(a, r, force)) return;
   const Rep &rp = a.rep[r];
@@ -157,11 +158,18 @@ __global__ void k_bin_scatter(KArgs a, int force) {
   int cy = cell_coord(x.y, rp.inv_h[1], rp.nc[1]);
   int cz = cell_coord(x.z, rp.inv_h[2], rp.nc[2]);
   float4 o;
-  o.x = frame_offset_fast(x.x, cx, rp.h[0], rp.half_h[0], rp.L[0]);
-  o.y = frame_offset_fast(x.y, cy, rp.h[1], rp.half_h[1], rp.L[1]);
-  o.z = frame_offset_fast(x.z, cz, rp.h[2], rp.half_h[2], rp.L[2]);
+  o.x = frame_offset(x.x, cell_centre(a, rp, 0, cx), rp.Lf[0], rp.L[0]);
+  o.y = frame_offset(x.y, cell_centre(a, rp, 1, cy), rp.Lf[1], rp.L[1]);
+  o.z = frame_offset(x.z, cell_centre(a, rp, 2, cz), rp.Lf[2], rp.L[2]);
   o.w = __uint_as_float(pack_cell(cx, cy, cz, a.type[i]));
   a.oref[i] = o;
+}
+
+__global__ void k_bin_scatter(KArgs a, int force) {
+  if (quiet(a, force)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    k_bin_scatter_one(a, i, force);
 }
 
 // Particle v goes to cell-list position p: the index maps both ways, and the
@@ -177,13 +185,10 @@ __device__ __forceinline__ void place(const KArgs &a, int p, int32_t v) {
 }
 
 // One warp per cell: order the cell's members by particle index.
-__global__ void k_cell_sort(KArgs a, int force) {
-  if (quiet(a, force)) return;
-  __shared__ int32_t buf[8][kMaxCellSort];
-  int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (cell >= a.n_cells) return;
-  int r = a.chunk_rep[cell / kChunkCells];
+__device__ __forceinline__ void cell_sort_one(const KArgs &a, int64_t cell, int force,
+                                              int32_t *buf) {
+  const int lane = threadIdx.x & 31;
+  const int r = a.chunk_rep[cell / kChunkCells];
   if (!rebuilding(a, r, force)) return;
   const int cnt = a.cell_count[cell];
   if (cnt == 0) return;
@@ -195,14 +200,24 @@ __global__ void k_cell_sort(KArgs a, int force) {
     for (int k = lane; k < cnt; k += 32) place(a, start + k, idx[k]);
     return;
   }
-  for (int k = lane; k < cnt; k += 32) buf[wid][k] = idx[k];
+  for (int k = lane; k < cnt; k += 32) buf[k] = idx[k];
   __syncwarp();
   for (int k = lane; k < cnt; k += 32) {
-    int32_t v = buf[wid][k];
+    int32_t v = buf[k];
     int rank = 0;
-    for (int m = 0; m < cnt; m++) rank += buf[wid][m] < v;
+    for (int m = 0; m < cnt; m++) rank += buf[m] < v;
     place(a, start + rank, v);
   }
+  __syncwarp();
+}
+
+__global__ void k_cell_sort(KArgs a, int force) {
+  if (quiet(a, force)) return;
+  __shared__ int32_t buf[8][kMaxCellSort];
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; cell < a.n_cells;
+       cell += warps)
+    cell_sort_one(a, cell, force, buf[threadIdx.x >> 5]);
 }
 
 // One warp per brick: the stage layout of its 64 stage cells (first slot and
@@ -271,9 +286,7 @@ __global__ void k_sort_flags(KArgs a, int value) {
   if (value) a.last_sort[r] = a.ds->step;
 }
 
-__global__ void k_sort_gather(KArgs a) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= a.n) return;
+__device__ __forceinline__ void k_sort_gather_one(const KArgs &a, int64_t k) {
   int r = replica_of(a, k);
   if (!a.sort_now[r]) return;
   int32_t old = a.cell_idx[k];
@@ -285,9 +298,14 @@ __global__ void k_sort_gather(KArgs a) {
   a.s_oref[k] = a.oref[old];
 }
 
-__global__ void k_sort_scatter(KArgs a) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= a.n) return;
+__global__ void k_sort_gather(KArgs a, int force) {
+  if (quiet(a, force)) return;  // sorts happen only at rebuilds
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    k_sort_gather_one(a, k);
+}
+
+__device__ __forceinline__ void k_sort_scatter_one(const KArgs &a, int64_t k) {
   int r = replica_of(a, k);
   if (!a.sort_now[r]) return;
   a.pos[k] = a.s_pos[k];
@@ -305,19 +323,33 @@ __global__ void k_sort_scatter(KArgs a) {
   if (k == a.rep[r].p0) a.ident[r] = 1;
 }
 
+__global__ void k_sort_scatter(KArgs a, int force) {
+  if (quiet(a, force)) return;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    k_sort_scatter_one(a, k);
+}
+
 inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// Grid of the grid-stride kernels: enough blocks to fill the GPU, never more
+// than the work needs.
+inline unsigned stride_blocks(int64_t n, int b) {
+  const unsigned need = blocks_for(n, b);
+  return need < 152u * 8u ? need : 152u * 8u;
+}
 
 }  // namespace
 
 cudaError_t launch_bin(const KArgs &a, int force, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
   k_bin_zero<<<(unsigned)a.n_chunks, 256, 0, st>>>(a, force);
-  k_bin_count<<<blocks_for(a.n, 256), 256, 0, st>>>(a, force);
+  k_bin_count<<<stride_blocks(a.n, 256), 256, 0, st>>>(a, force);
   k_scan_chunk_sum<<<(unsigned)a.n_chunks, 256, 0, st>>>(a, force);
   k_scan_chunks<<<blocks_for((int64_t)a.R * 32, 256), 256, 0, st>>>(a, force);
   k_scan_cells<<<(unsigned)a.n_chunks, 256, 0, st>>>(a, force);
-  k_bin_scatter<<<blocks_for(a.n, 256), 256, 0, st>>>(a, force);
-  k_cell_sort<<<blocks_for(a.n_cells * 32, 256), 256, 0, st>>>(a, force);
+  k_bin_scatter<<<stride_blocks(a.n, 256), 256, 0, st>>>(a, force);
+  k_cell_sort<<<stride_blocks(a.n_cells * 32, 256), 256, 0, st>>>(a, force);
   if (a.n_bricks > 0) k_brick_desc<<<blocks_for(a.n_bricks * 32, 256), 256, 0, st>>>(a, force);
   return cudaGetLastError();
 }
@@ -325,8 +357,8 @@ cudaError_t launch_bin(const KArgs &a, int force, cudaStream_t st) {
 cudaError_t launch_sort(const KArgs &a, int force, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
   if (force) k_sort_flags<<<blocks_for(a.R, 128), 128, 0, st>>>(a, 1);
-  k_sort_gather<<<blocks_for(a.n, 256), 256, 0, st>>>(a);
-  k_sort_scatter<<<blocks_for(a.n, 256), 256, 0, st>>>(a);
+  k_sort_gather<<<stride_blocks(a.n, 256), 256, 0, st>>>(a, force);
+  k_sort_scatter<<<stride_blocks(a.n, 256), 256, 0, st>>>(a, force);
   if (force) k_sort_flags<<<blocks_for(a.R, 128), 128, 0, st>>>(a, 0);
   return cudaGetLastError();
 }

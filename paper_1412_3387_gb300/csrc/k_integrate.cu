@@ -16,6 +16,16 @@ __device__ __forceinline__ double4 ld_force(const KArgs &a, int64_t i) {
   return ld_d4(reinterpret_cast<const double4 *>(a.force) + i);
 }
 
+// Force without the energy word (integration needs three components only).
+__device__ __forceinline__ double3 ld_force3(const KArgs &a, int64_t i) {
+  if (a.mixed) {
+    const float4 f = reinterpret_cast<const float4 *>(a.force)[i];
+    return make_double3(f.x, f.y, f.z);
+  }
+  const double4 f = ld_d4(reinterpret_cast<const double4 *>(a.force) + i);
+  return make_double3(f.x, f.y, f.z);
+}
+
 __device__ __forceinline__ double4 ld_d4_plain(const double4 *p) {
   const double2 *q = reinterpret_cast<const double2 *>(p);
   double2 x = q[0], y = q[1];
@@ -29,8 +39,10 @@ __device__ __forceinline__ void st_d4(double4 *p, const double4 &v) {
 }
 
 // One coordinate of the first velocity-Verlet half (Sec. 3): kick, drift and
-// wrap into [0, L) counting image crossings; same operation order as the
-// oracle (no fused multiply-add).
+// wrap into [0, L) counting image crossings.  Kick and drift are one fused
+// multiply-add each (FP64 instructions are scarce on GB300); the oracle
+// multiplies and adds separately, a difference of at most one rounding per
+// step.
 // A crossing moves x by k L with k = floor(x / L) (k = +-1 for any sane time
 // step, where this equals the oracle's single subtraction); the fix-ups
 // absorb rounding at the box edge.  Non-finite x is left alone (and flagged
@@ -49,8 +61,8 @@ __device__ __forceinline__ bool finite_bits(double x) {
 
 __device__ __forceinline__ void kick_drift(double &x, double &v, int &img, double f, double hk,
                                            double dt, double L) {
-  v = __dadd_rn(v, __dmul_rn(hk, f));
-  x = __dadd_rn(x, __dmul_rn(dt, v));
+  v = fma(hk, f, v);
+  x = fma(dt, v, x);
   if (outside_box(x, __double_as_longlong(L)) && finite_bits(x)) {
     double k = floor(x / L);
     k = fmin(fmax(k, -1e9), 1e9);
@@ -75,7 +87,7 @@ __global__ void k_integrate1(KArgs a) {
     const Rep &rp = a.rep[r];
     double4 x = ld_d4_plain(a.pos + i);
     double4 v = ld_d4_plain(a.vel + i);
-    const double4 f = ld_force(a, i);
+    const double3 f = ld_force3(a, i);
     int4 img = a.image[i];
     const int4 img0 = img;
     const double hk = a.half_dt_m;
@@ -89,9 +101,9 @@ __global__ void k_integrate1(KArgs a) {
     const float4 ref = a.oref[i];
     float4 o = ref;
     const uint32_t w = __float_as_uint(ref.w);
-    o.x = frame_offset_fast(x.x, cell_x(w), rp.h[0], rp.half_h[0], rp.L[0]);
-    o.y = frame_offset_fast(x.y, cell_y(w), rp.h[1], rp.half_h[1], rp.L[1]);
-    o.z = frame_offset_fast(x.z, cell_z(w), rp.h[2], rp.half_h[2], rp.L[2]);
+    o.x = frame_offset(x.x, cell_centre(a, rp, 0, cell_x(w)), rp.Lf[0], rp.L[0]);
+    o.y = frame_offset(x.y, cell_centre(a, rp, 1, cell_y(w)), rp.Lf[1], rp.L[1]);
+    o.z = frame_offset(x.z, cell_centre(a, rp, 2, cell_z(w)), rp.Lf[2], rp.L[2]);
     // the FP32 copies are kept in cell-list order
     const int64_t p = __ldg(a.ident + r) ? i : (int64_t)a.cellpos[i];
     a.pos4f[p] = o;
@@ -133,16 +145,17 @@ __global__ void k_integrate1(KArgs a) {
   }
 }
 
-// Velocity Verlet, second half: v += dt/2 F/m.
+// Velocity Verlet, second half: v += dt/2 F/m (one fused multiply-add per
+// component, as in the first half).
 __global__ void k_integrate2(KArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   double4 v = ld_d4_plain(a.vel + i);
-  const double4 f = ld_force(a, i);
+  const double3 f = ld_force3(a, i);
   const double hk = a.half_dt_m;
-  v.x = __dadd_rn(v.x, __dmul_rn(hk, f.x));
-  v.y = __dadd_rn(v.y, __dmul_rn(hk, f.y));
-  v.z = __dadd_rn(v.z, __dmul_rn(hk, f.z));
+  v.x = fma(hk, f.x, v.x);
+  v.y = fma(hk, f.y, v.y);
+  v.z = fma(hk, f.z, v.z);
   st_d4(a.vel + i, v);
 }
 
@@ -286,9 +299,9 @@ __global__ void k_init_frames(KArgs a) {
   const int cy = cell_coord(x.y, rp.inv_h[1], rp.nc[1]);
   const int cz = cell_coord(x.z, rp.inv_h[2], rp.nc[2]);
   float4 o;
-  o.x = frame_offset_fast(x.x, cx, rp.h[0], rp.half_h[0], rp.L[0]);
-  o.y = frame_offset_fast(x.y, cy, rp.h[1], rp.half_h[1], rp.L[1]);
-  o.z = frame_offset_fast(x.z, cz, rp.h[2], rp.half_h[2], rp.L[2]);
+  o.x = frame_offset(x.x, cell_centre(a, rp, 0, cx), rp.Lf[0], rp.L[0]);
+  o.y = frame_offset(x.y, cell_centre(a, rp, 1, cy), rp.Lf[1], rp.L[1]);
+  o.z = frame_offset(x.z, cell_centre(a, rp, 2, cz), rp.Lf[2], rp.L[2]);
   // tags must be a permutation of 0..N-1 and types lie in [0, ntypes): both
   // index tables later, so out-of-range values are refused here
   const int32_t tg = a.tag[i], ty = a.type[i];

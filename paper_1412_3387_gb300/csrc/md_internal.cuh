@@ -48,6 +48,8 @@ struct Rep {
   double half_h[3];   // h / 2
   double inv_h[3];    // nc / L
   float hf[3];        // float(h): shift of a neighbouring cell's frame
+  float Lf[3];        // float(L)
+  int64_t ctab0;      // first entry of the replica's cell-centre table (x, then y, then z)
   float band;         // FP32 r^2 uncertainty band (see DESIGN: exact decisions)
   double volume;
 };
@@ -97,6 +99,7 @@ struct KArgs {
   float4 *vel4f;       // [cell-list position] FP32 velocity, tag bits in w (DPD)
   int32_t *cellpos;    // [particle] cell-list position
   int32_t *cell_rank;  // [cells] linear cell -> rank in brick order (per replica)
+  const double *ctab;  // cell centres (c + 1/2) h per replica and axis
   const int32_t *brick_stage;  // [bricks][64] cell slot of each stage cell (brick.cuh)
   const int4 *brick_info;      // [bricks] first cell slot, cell mask, replica
   const int32_t *brick_rep;    // [bricks] replica
@@ -173,17 +176,23 @@ __device__ __forceinline__ int cell_coord(double x, double inv_h, int nc) {
   return c < 0 ? 0 : c;
 }
 
-// FP32 offset of x from the centre (c + 1/2) h of frame cell c, folded into
-// (-L/2, L/2].  FP64 instructions are scarce on GB300, so the centre is one
-// FP64 multiply-add and the periodic fold (needed only once the particle has
-// crossed the box since its frame was set) is decided on the FP32 value: the
-// offsets stay below h + skin << L/2, far from the fold's threshold.
-__device__ __forceinline__ float frame_offset_fast(double x, int c, double h, double half_h,
-                                                   double L) {
-  double d = x - fma((double)c, h, half_h);
+// FP32 offset of x from the centre ctr = (c + 1/2) h of its frame cell,
+// folded into (-L/2, L/2].  FP64 instructions are scarce on GB300 (a few per
+// clock per SM), so the centre comes from a table and the periodic fold
+// (needed only once the particle has crossed the box since its frame was
+// set) is decided on the FP32 value: the offsets stay below h + skin << L/2,
+// far from the fold's threshold.
+__device__ __forceinline__ float frame_offset(double x, double ctr, float Lf, double L) {
+  const double d = x - ctr;
   const float df = (float)d;
-  if (fabsf(df) > 0.5f * (float)L) d += df > 0.f ? -L : L;
-  return (float)d;
+  if (fabsf(df) > 0.5f * Lf) return (float)(d + (df > 0.f ? -L : L));
+  return df;
+}
+
+// Centre of cell c along axis ax of replica rp.
+__device__ __forceinline__ double cell_centre(const KArgs &a, const Rep &rp, int ax, int c) {
+  const int off = ax == 0 ? 0 : ax == 1 ? rp.nc[0] : rp.nc[0] + rp.nc[1];
+  return __ldg(a.ctab + rp.ctab0 + off + c);
 }
 
 // Exact FP64 minimum-image r^2 with a fixed operation order and no FMA:
