@@ -136,9 +136,10 @@ struct BrickSmem {
   unsigned char *base;
   int cap;
   bool vel;
+  __host__ __device__ static int pitch(int cap) { return cap + 1; }
   __host__ __device__ static size_t desc_bytes() { return 3 * sizeof(BrickDesc); }
   __host__ __device__ static size_t stage_bytes(int cap, bool vel) {
-    return (size_t)2 * (cap + 1) * sizeof(float4) * (vel ? 2 : 1);
+    return (size_t)2 * pitch(cap) * sizeof(float4) * (vel ? 2 : 1);
   }
   __host__ __device__ static size_t bytes(int cap, bool vel, size_t scratch) {
     return desc_bytes() + stage_bytes(cap, vel) + scratch;
@@ -147,10 +148,10 @@ struct BrickSmem {
     return reinterpret_cast<BrickDesc *>(base)[t % 3];
   }
   __device__ __forceinline__ float4 *pos(long long t) const {
-    return reinterpret_cast<float4 *>(base + desc_bytes()) + (t & 1) * (cap + 1);
+    return reinterpret_cast<float4 *>(base + desc_bytes()) + (t & 1) * pitch(cap);
   }
   __device__ __forceinline__ float4 *vel4(long long t) const {
-    return reinterpret_cast<float4 *>(base + desc_bytes()) + (2 + (t & 1)) * (cap + 1);
+    return reinterpret_cast<float4 *>(base + desc_bytes()) + (2 + (t & 1)) * pitch(cap);
   }
   __device__ __forceinline__ unsigned char *scratch() const {
     return base + desc_bytes() + stage_bytes(cap, vel);

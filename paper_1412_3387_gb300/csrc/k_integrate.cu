@@ -341,7 +341,8 @@ __global__ void k_export_forces(KArgs a, double *f, double *v) {
 }
 
 // One warp per brick: decode each row's stage slots into particle indices and
-// write them at the particle's own row.
+// write them, compacted, at the particle's own row (rows in the tile layout
+// can hold sentinel gaps).
 __global__ void k_export_nlist(KArgs a, int32_t *counts, int32_t *rows) {
   const int lane = threadIdx.x & 31;
   const int64_t b = blockIdx.x;
@@ -350,18 +351,24 @@ __global__ void k_export_nlist(KArgs a, int32_t *counts, int32_t *rows) {
   for (int q = 0; q < d.nhome; q++) {
     const int p = d.hstart + q;
     const int32_t i = a.cell_idx[p];
-    const int nn = a.n_nb[p];
     const int jg = q / P, q2 = q % P, pj = min(P, d.nhome - jg * P);
     const uint16_t *grp = a.nl + (size_t)(d.hstart + jg * P) * (size_t)a.max_nb;
-    if (lane == 0) counts[i] = nn;
-    for (int k = lane; k < a.max_nb; k += 32) {
-      int32_t j = -1;
-      if (k < nn) {
-        const int e = grp[(((k >> lw) * pj + q2) << lw) + (k & (W - 1))];
-        if (e > 0) j = a.cell_idx[d.start[stage_cell_of(d, e - 1)] + (e - 1 - d.off[stage_cell_of(d, e - 1)])];
+    const int T = a.nl_tiles[d.hstart + jg * P];
+    if (lane == 0) counts[i] = a.n_nb[p];
+    int n = 0;  // entries written so far (the same in every lane)
+    for (int k0 = 0; k0 < T * W; k0 += 32) {
+      const int k = k0 + lane;
+      int e = 0;
+      if (k < T * W) e = grp[((k >> lw) * pj + q2) * W + (k & (W - 1))];
+      const unsigned m = __ballot_sync(0xffffffffu, e > 0);
+      if (e > 0) {
+        const int at = n + __popc(m & ((1u << lane) - 1u));
+        const int s = e - 1, c = stage_cell_of(d, s);
+        if (at < a.max_nb) rows[(int64_t)i * a.max_nb + at] = a.cell_idx[d.start[c] + (s - d.off[c])];
       }
-      rows[(int64_t)i * a.max_nb + k] = j;
+      n += __popc(m);
     }
+    for (int k = n + lane; k < a.max_nb; k += 32) rows[(int64_t)i * a.max_nb + k] = -1;
   }
 }
 

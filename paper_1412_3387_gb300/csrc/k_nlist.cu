@@ -7,12 +7,13 @@
 // other tuning parameter).  A particle's candidates are the members of the
 // 27 cells around its cell: a 3 x 3 x 3 sub-block of the stage, i.e. nine
 // contiguous runs of slots.  The W lanes of a particle split every run into W
-// contiguous parts; each lane appends its hits to a row in its own
-// shared-memory scratch, so the candidate loop is a straight line (stage load,
-// distance, compare, branch-free append).  The W partial rows of a particle,
-// concatenated in lane order, form its row (a fixed, deterministic order), and
-// are written out, coalesced, in the pair kernel's group-tile layout
-// (brick.cuh) with the sentinel padding.
+// contiguous parts.  After each block of U candidates the lanes of a
+// particle take an exclusive prefix sum of their hit counts and write their
+// hits straight into the row, in the pair kernel's tile layout (brick.cuh);
+// rows are then padded with the sentinel up to their group's tile count.
+// Rows thus come out compact and in a fixed, deterministic order (block by
+// block; within a block, lane by lane, each lane's hits in slot order) with
+// no scratch storage.
 //
 // Distance test.  Candidates are screened in FP32; a candidate whose FP32 r^2
 // lies within a proven error band of r_list^2 is re-tested with the FP64
@@ -28,17 +29,9 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// Scratch of one warp: 32 partial rows of max_nb + 1 entries, stored entry
-// by entry across the lanes (entry k of lane l at k * 32 + l, so the lanes'
-// appends fall in different banks), then the lanes' row lengths and their
-// offsets inside the particle's row.
-__host__ __device__ inline size_t warp_scratch_bytes(int max_nb) {
-  return ((size_t)32 * (max_nb + 1) * 2 + 64 * 4 + 15) / 16 * 16;
-}
-
 template <int WB, bool DIRECT>
 __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, const float4 *spos,
-                                           uint16_t *scr, int *meta, int j) {
+                                           int j) {
   constexpr int PB = 32 / WB;
   constexpr int U = 8;
   const int lane = threadIdx.x & 31;
@@ -54,126 +47,109 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
   const float4 oi = src.pos((uint32_t)(hs.slot + 1));
   const float lo2 = a.rl2f - rp.band, hi2 = a.rl2f + rp.band;
   const int max_nb = a.max_nb;
-  uint16_t *row = scr + lane;  // entry k at row[k * 32]
-  const uint32_t row_s = smem_u32(row);
+  // the pair kernel's row layout: groups of Pp = 32 / Wp particles, tiles of
+  // Wp columns per particle; this lane owns RC = Wp / WB of the columns of its
+  // particle and puts its n-th hit in column n mod RC, tile n / RC
+  // the pair kernel's row layout: groups of Pp = 32 / Wp particles, tiles of
+  // Wp entries per particle; the row's entry k sits in tile k / Wp, column k % Wp
+  const int lwp = a.w_store_log2, Wp = 1 << lwp, Pp = 32 >> lwp;
+  const int tcap = max_nb >> lwp;  // tiles a row region holds
+  const int gq = j * PB + qe;      // the particle's place in the brick
+  const int grp = gq / Pp, q2 = gq - grp * Pp;
+  const int pj = min(Pp, d.nhome - grp * Pp);
+  uint16_t *gbase = a.nl + (size_t)(d.hstart + grp * Pp) * (size_t)max_nb;
+  auto put = [&](int k, uint16_t v) {
+    const int t = k >> lwp;
+    if (t < tcap) gbase[((t * pj + q2) << lwp) + (k & (Wp - 1))] = v;
+  };
   // the nine runs of the particle's 3 x 3 x 3 stencil: stage cells
   // (hx .. hx + 2, hy + dy, hz + dz) for the home cell (hx + 1, hy + 1, hz + 1)
   const int c0 = (hs.s & 3) - 1 + 4 * (((hs.s >> 2) & 3) - 1) + 16 * ((hs.s >> 4) - 1);
-  int n = 0;
+  int n = 0;  // row length so far (the same in the particle's WB lanes)
   for (int rr = 0; rr < 9; rr++) {
     const int s = c0 + 4 * (rr % 3) + 16 * (rr / 3);
     const int rlo = d.off[s], len = d.off[s + 3] - rlo;
     // this lane's part of the run; all lanes take part in every run, and the
-    // loop runs to the warp's longest part so that the warp-wide vote below
-    // sees every lane
+    // loop runs to the warp's longest part so that the warp-wide vote and the
+    // shuffles below see every lane
     const int part = (len + WB - 1) / WB;
     const int beg = rlo + sl * part;
-    const int mylen = min(max(len - sl * part, 0), part);
+    const int mylen = active ? min(max(len - sl * part, 0), part) : 0;
     const int wlen = (int)__reduce_max_sync(FULL, (unsigned)mylen);
     for (int x0 = 0; x0 < wlen; x0 += U) {
-      const int n0 = n;
-      bool band = false;
-      // all loads of the group first: the appends below store to shared
-      // memory, which the compiler would otherwise not let later loads pass
       float4 oju[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const int slot = beg + x0 + u;
-        const bool valid = active && x0 + u < mylen && slot != hs.slot;
+        const bool valid = x0 + u < mylen && slot != hs.slot;
         oju[u] = src.pos(valid ? (uint32_t)(slot + 1) : 0u);
       }
+      bool band = false;
+      unsigned m = 0u;  // bit u: candidate x0 + u is a neighbour
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const float4 oj = oju[u];
         const float dx = oi.x - oj.x, dy = oi.y - oj.y, dz = oi.z - oj.z;
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         band |= (r2 >= lo2) & (r2 < hi2);
-        // branch-free append: the store is kept only if the count moves on
-        // (the scratch row has room for max_nb + 1 entries)
-        sts16(row_s + (uint32_t)min(n, max_nb) * 64u, (uint16_t)(beg + x0 + u + 1));
-        n += r2 < lo2 ? 1 : 0;
+        m |= (r2 < lo2 ? 1u : 0u) << u;
       }
       if (__any_sync(FULL, band)) {
-        // rare: redo the group in order, deciding band candidates in FP64 with
-        // the oracle's operation order
-        n = n0;
+        // rare: decide the block's band candidates in FP64 with the oracle's
+        // operation order
         const int32_t i = ident ? p : __ldg(a.cell_idx + p);
         for (int u = 0; u < U; u++) {
           const int slot = beg + x0 + u;
-          const bool valid = active && x0 + u < mylen && slot != hs.slot;
-          if (!valid) continue;
+          if (!(x0 + u < mylen && slot != hs.slot)) continue;
           const float4 oj = src.pos((uint32_t)(slot + 1));
           const float dx = oi.x - oj.x, dy = oi.y - oj.y, dz = oi.z - oj.z;
           const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          bool hit = r2 < lo2;
           if (r2 >= lo2 && r2 < hi2) {
             double dd[3];
-            hit = exact_r2(ld_d4(a.pos + i), ld_d4(a.pos + src.index((uint32_t)(slot + 1), ident)),
-                           rp, dd) < a.rl2;
-          }
-          if (hit) {
-            if (n < max_nb) row[n * 32] = (uint16_t)(slot + 1);
-            n++;
+            const bool hit = exact_r2(ld_d4(a.pos + i),
+                                      ld_d4(a.pos + src.index((uint32_t)(slot + 1), ident)), rp,
+                                      dd) < a.rl2;
+            m |= (hit ? 1u : 0u) << u;
           }
         }
       }
+      // compact: this lane's hits follow those of the particle's lower lanes
+      const int h = __popc(m);
+      int incl = h;
+#pragma unroll
+      for (int o = 1; o < WB; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o);
+        if (sl >= o) incl += v;
+      }
+      const int tot = __shfl_sync(FULL, incl, lane | (WB - 1));
+      int k = n + incl - h;
+      while (m) {
+        const int u = __ffs(m) - 1;
+        m &= m - 1u;
+        put(k++, (uint16_t)(beg + x0 + u + 1));
+      }
+      n += tot;
     }
   }
 
-  // row length of each particle and each lane's offset inside it
-  int incl = n;
-#pragma unroll
-  for (int o = 1; o < WB; o <<= 1) {
-    const int y = __shfl_up_sync(FULL, incl, o);
-    if (sl >= o) incl += y;
-  }
-  const int nq = __shfl_sync(FULL, incl, qq * WB + WB - 1);
-  int *mpre = meta, *mcnt = meta + 32;
-  mpre[lane] = incl - n;
-  mcnt[lane] = n;
+  // tiles of the particle and of its pair group (Pp particles = Pp * WB
+  // aligned lanes of this warp)
+  const int tq = active ? (n + Wp - 1) >> lwp : 0;
+  int tg = tq;
+  const int glanes = Pp * WB;
+  for (int o = 1; o < glanes; o <<= 1) tg = max(tg, __shfl_xor_sync(FULL, tg, o));
+  tg = min(tg, tcap);
   if (active && sl == 0) {
-    a.n_nb[p] = nq;
-    if (nq > max_nb) {
-      atomicMax(&a.ds->need_max_nb, nq);
+    a.n_nb[p] = n;
+    if (tq > tcap) {
+      atomicMax(&a.ds->need_max_nb, tq * Wp);
       set_error(a.ds, kErrNlistOverflow);
     }
   }
-  __syncwarp();
-
-  // write the pass's rows as the pair kernel's row groups (Pp = 32 / Wp
-  // particles each; WB <= Wp, so a pass holds whole groups)
-  const int lwp = a.w_store_log2, Wp = 1 << lwp, Pp = 32 >> lwp;
-  for (int h = 0; h < PB; h += Pp) {
-    const int pj = min(Pp, d.nhome - (j * PB + h));
-    if (pj <= 0) break;
-    const int mine = (active && qq >= h && qq < h + pj) ? min(nq, max_nb) : 0;
-    const int mx = (int)__reduce_max_sync(FULL, (unsigned)mine);
-    const int T = (mx + Wp - 1) >> lwp;
-    const int pg = d.hstart + j * PB + h;
-    if (lane == 0) a.nl_tiles[pg] = T;
-    uint16_t *out = a.nl + (size_t)pg * (size_t)max_nb;
-    const int E = T * pj * Wp;
-    const int lpp = 5 - lwp;  // log2 Pp: a full group's tile is 32 entries
-    for (int e = lane; e < E; e += 32) {
-      const int slp = e & (Wp - 1), rest = e >> lwp;
-      const int q2 = pj == Pp ? (rest & (Pp - 1)) : rest % pj;
-      const int t = pj == Pp ? (rest >> lpp) : rest / pj;
-      const int k = (t << lwp) + slp;
-      const int l0 = (h + q2) * WB;  // first lane of the particle's segment
-      const int nqb = mpre[l0 + WB - 1] + mcnt[l0 + WB - 1];
-      uint16_t v = 0;
-      if (k < min(nqb, max_nb)) {
-        int sb = 0;
-#pragma unroll
-        for (int t2 = 1; t2 < WB; t2++)
-          if (mpre[l0 + t2] <= k) sb = t2;
-        const int off = k - mpre[l0 + sb];
-        if (off < max_nb) v = scr[(size_t)off * 32 + (l0 + sb)];
-      }
-      out[e] = v;
-    }
-  }
-  __syncwarp();
+  if (active && q2 == 0 && sl == 0) a.nl_tiles[d.hstart + grp * Pp] = tg;
+  // sentinel padding of the row up to the group's tile count
+  if (active)
+    for (int k = n + sl; k < (tg << lwp); k += WB) put(k, 0);
 }
 
 // Persistent over bricks b = blockIdx + t G (replicas that do not rebuild are
@@ -191,9 +167,6 @@ __global__ void __launch_bounds__(kMaxBrickThreads) k_nlist(KArgs a, int cap, in
   }
   const BrickSmem M{smem, cap, false};
   const int warp = threadIdx.x >> 5, C = blockDim.x >> 5;
-  unsigned char *mine = M.scratch() + (size_t)warp * warp_scratch_bytes(a.max_nb);
-  uint16_t *scr = reinterpret_cast<uint16_t *>(mine);
-  int *meta = reinterpret_cast<int *>(mine + (size_t)32 * (a.max_nb + 1) * 2);
   const long long G = gridDim.x;
   // the bricks this block builds (rebuilding replicas only)
   auto wanted = [&](long long b) {
@@ -233,9 +206,9 @@ __global__ void __launch_bounds__(kMaxBrickThreads) k_nlist(KArgs a, int cap, in
     const BrickDesc &d = M.desc(t);
     const int ng = (d.nhome + PB - 1) / PB;
     if (d.off[64] > cap) {
-      for (int j = warp; j < ng; j += C) build_pass<WB, true>(a, d, M.pos(t), scr, meta, j);
+      for (int j = warp; j < ng; j += C) build_pass<WB, true>(a, d, M.pos(t), j);
     } else {
-      for (int j = warp; j < ng; j += C) build_pass<WB, false>(a, d, M.pos(t), scr, meta, j);
+      for (int j = warp; j < ng; j += C) build_pass<WB, false>(a, d, M.pos(t), j);
     }
     if (has2) {
       uint4 *dst = reinterpret_cast<uint4 *>(&M.desc(t + 2));
@@ -251,31 +224,20 @@ __global__ void __launch_bounds__(kMaxBrickThreads) k_nlist(KArgs a, int cap, in
   }
 }
 
-// Computing warps that fit beside the stage (each needs its row scratch).
-inline int fitting_warps(const KArgs &a, int want) {
-  const size_t ring = BrickSmem::bytes(a.stage_cap, false, 0);
-  const size_t per = warp_scratch_bytes(a.max_nb);
-  const int fit = ring >= 227u * 1024u ? 0 : (int)((227u * 1024u - ring) / per);
-  return std::min(want, fit);
-}
-
 template <int WB>
 cudaError_t launch_w(const KArgs &a, int block, int force, cudaStream_t st) {
-  const int C = fitting_warps(a, block / 32);  // large max_nb: fewer warps
-  if (C < 1) return cudaErrorInvalidConfiguration;
-  const size_t smem = BrickSmem::bytes(a.stage_cap, false, (size_t)C * warp_scratch_bytes(a.max_nb));
-  const int threads = 32 * C;
-  const int grid = persistent_grid((const void *)k_nlist<WB>, threads, smem, a.n_bricks);
+  const size_t smem = BrickSmem::bytes(a.stage_cap, false, 0);
+  const int grid = persistent_grid((const void *)k_nlist<WB>, block, smem, a.n_bricks);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
-  k_nlist<WB><<<grid, threads, smem, st>>>(a, a.stage_cap, force);
+  k_nlist<WB><<<grid, block, smem, st>>>(a, a.stage_cap, force);
   return cudaGetLastError();
 }
 
 template <int WB>
-int max_block_w(const KArgs &a) {
+int max_block_w(const KArgs &) {
   cudaFuncAttributes at;
   if (cudaFuncGetAttributes(&at, k_nlist<WB>) != cudaSuccess) return 0;
-  return 32 * fitting_warps(a, at.maxThreadsPerBlock / 32);
+  return at.maxThreadsPerBlock;
 }
 
 template <int WB>
