@@ -134,14 +134,16 @@ md_status md_set_bonds(md_system *s, const int32_t *bond_tags, int64_t n_bonds,
                        double K, double r0, md_stream stream);
 
 /* Space-filling-curve sort: reorders every caller particle array so that
- * particles follow the Hilbert order of their cells, ties by current index.
+ * particles follow the Hilbert order of their cells, then the binning's
+ * order inside each cell (by x offset, then index).
  * force = 0: only replicas that rebuild now and whose last sort is
  * >= sort_period steps old.  Requires md_build_cells to have binned the
  * current positions (it sorts by that binning). */
 md_status md_sort_particles(md_system *s, int32_t force, md_stream stream);
 
 /* Cell-list binning (Sec. 4.3.3, Sec. 5.1): counts per cell, exclusive scan,
- * scatter, then particles ordered by index inside each cell.  force = 0: only
+ * scatter, then the members of each cell ordered by their FP32 x offset from
+ * the cell centre, ties by particle index.  force = 0: only
  * replicas whose rebuild flag was raised by md_integrate(half = 1).  The
  * neighbour list refers to the binning it was built from: after a forced
  * binning, md_compute_pair returns MD_ERR_STATE until md_build_nlist ran. */
@@ -151,7 +153,11 @@ md_status md_build_cells(md_system *s, int32_t force, md_stream stream);
  * the 27 cells around it and compact every j != i with
  * |x_i - x_j|^2 < (r_cut + r_skin)^2 (minimum image, FP64 decision) into
  * row i.  Records the build positions for the half-buffer test.
- * force = 0: only replicas whose rebuild flag is raised.
+ * force = 0: only replicas whose rebuild flag is raised.  The build reads the
+ * binning's member order; if particles moved through this API since the last
+ * md_build_cells (md_integrate, md_step, md_run), it bins them again first.
+ * After writing positions into the particle arrays directly, call
+ * md_build_cells before this.
  * Row overflow: MD_ERR_NLIST_OVERFLOW in the device error word. */
 md_status md_build_nlist(md_system *s, int32_t force, md_stream stream);
 
@@ -189,8 +195,8 @@ md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream st
 /* Autotuner (Sec. 5.2): for the pair and neighbour-list kernels, times every
  * (block size b = 32 k <= 512, threads per particle w = 2^m <= 32) pair with
  * the median of n_samples launches (paper: 5), and keeps the fastest.  Both
- * kernels are persistent and b counts their computing threads (each block has
- * one more warp that streams data into shared memory).  The list build's w is
+ * kernels are persistent: a block keeps one brick's data in shared memory
+ * while the next brick's is copied in.  The list build's w is
  * at most the pair kernel's (the pair kernel's w fixes the list layout, and a
  * build pass must cover whole row groups of it).  block_stride (>= 1) thins
  * the block sizes to every block_stride-th multiple of 32.  Synchronises
@@ -198,8 +204,8 @@ md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream st
 md_status md_autotune(md_system *s, int32_t n_samples, int32_t block_stride,
                       md_stream stream);
 
-/* Sets / reads the launch parameters of one kernel (md_kernel): b computing
- * threads (a multiple of 32, at most the kernel's limit) and w threads per
+/* Sets / reads the launch parameters of one kernel (md_kernel): b threads per
+ * block (a multiple of 32, at most the kernel's limit) and w threads per
  * particle.  Changing the pair kernel's w changes the list layout and forces
  * a rebuild; a list-build w above the pair kernel's runs at the pair
  * kernel's. */

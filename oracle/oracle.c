@@ -494,11 +494,12 @@ uint64_t orc_hilbert3(uint32_t x, uint32_t y, uint32_t z, int32_t bits) {
     return h;
 }
 
-typedef struct { uint64_t key; int64_t idx; } keyidx_t;
+typedef struct { uint64_t key; float xo; int64_t idx; } keyidx_t;
 
 static int cmp_keyidx(const void *a, const void *b) {
     const keyidx_t *x = a, *y = b;
     if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->xo != y->xo) return x->xo < y->xo ? -1 : 1;
     return (x->idx > y->idx) - (x->idx < y->idx);
 }
 
@@ -523,6 +524,12 @@ void orc_sfc_order(int64_t n, const double *pos, const double *L, double r_list,
         for (int k = 0; k < 3; k++) c[k] = (uint32_t)cell_of(pos[4 * i + k], nc[k], L[k]);
         const uint64_t brick = orc_hilbert3(c[0] >> 1, c[1] >> 1, c[2] >> 1, bits);
         ki[i].key = brick * 8u + (c[0] & 1u) + 2u * (c[1] & 1u) + 4u * (c[2] & 1u);
+        /* inside a cell: by the x offset from the cell centre (c + 1/2) h,
+         * minimum image, rounded to FP32; then by index */
+        const double h = L[0] / nc[0];
+        double d = pos[4 * i] - fma((double)c[0], h, 0.5 * h);
+        d -= L[0] * rint(d / L[0]);
+        ki[i].xo = (float)d;
         ki[i].idx = i;
     }
     qsort(ki, (size_t)n, sizeof(keyidx_t), cmp_keyidx);

@@ -130,8 +130,8 @@ uint64_t orc_hilbert3(uint32_t x, uint32_t y, uint32_t z, int32_t bits);
 
 /* Space-filling-curve order: particles ordered by the Hilbert index of the
  * brick of 2 x 2 x 2 cells holding their cell (cell list of minimum width
- * r_list), then by the cell's place in the brick (x, then y, then z), ties
- * by index. */
+ * r_list), then by the cell's place in the brick (x, then y, then z); inside
+ * a cell by the x offset from the cell centre (FP32), then by index. */
 void orc_sfc_order(int64_t n, const double *pos, const double *L, double r_list,
                    int32_t *order);
 

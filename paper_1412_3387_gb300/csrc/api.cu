@@ -27,6 +27,10 @@ struct md_system {
   bool built = false;   // list built and forces computed (ready to step)
   bool binned = false;  // cells binned at least once
   bool listed = false;  // list built in the current layout
+  // The binning is current (no particle moved since): for every replica, or
+  // for the replicas that rebuild.  The list build needs it (it searches
+  // x-windows in the cells' member order).
+  bool bin_all = false, bin_cond = false;
   int64_t step = 0;
   int64_t n_bonds = 0;
   cudaStream_t cap = nullptr;
@@ -171,15 +175,17 @@ md_status make_plan(const md_params *p, Plan &pl) {
     chunk0 += rp.nchunk;
     tchunk0 += rp.ntchunk;
   }
-  // Brick stage buffers (brick.cuh): room for about 20 % more than the mean
-  // population of the 64 stage cells of the densest replica; a brick beyond
-  // that is served from global memory instead.  Two buffers (positions, and
-  // velocities for mixed-precision DPD) must fit well inside shared memory.
+  // Brick stage buffers (brick.cuh): room for the mean population m of the 64
+  // stage cells of the densest replica plus six Poisson standard deviations
+  // (a liquid fluctuates less); a brick beyond that is served from global
+  // memory instead.  Two buffers (positions, and velocities for
+  // mixed-precision DPD) must fit well inside shared memory.
   double dens = 0.0;
   for (const Rep &rp : pl.reps)
     if (rp.ncell > 0) dens = std::max(dens, (double)(rp.p1 - rp.p0) / rp.ncell);
   const bool vel = p->pair == MD_PAIR_DPD && p->precision == MD_MIXED;
-  int cap = (int)std::ceil((1.2 * 64.0 * dens + 64.0) / 32.0) * 32;
+  const double m = 64.0 * dens;
+  int cap = (int)std::ceil((m + 6.0 * std::sqrt(m) + 64.0) / 32.0) * 32;
   cap = std::min(cap, 64 * kMaxCellSort);
   while (BrickSmem::bytes(cap, vel, 0) > 160u * 1024u) cap /= 2;
   pl.stage_cap = std::max(cap, 32);
@@ -255,7 +261,7 @@ md_status enqueue_step(md_system *s, int want_virial, cudaStream_t st) {
 md_status prepare(md_system *s, cudaStream_t st) {
   if (s->built) return MD_OK;
   MD_CUDA(launch_bin(s->a, 1, st));
-  s->binned = true;
+  s->binned = s->bin_all = s->bin_cond = true;
   MD_CUDA(launch_nlist(s->a, s->tune[MD_KERNEL_NLIST], 1, st));
   s->listed = true;
   MD_CUDA(launch_pair(s->a, s->tune[MD_KERNEL_PAIR], 0, st));
@@ -620,8 +626,9 @@ md_status md_sort_particles(md_system *s, int32_t force, md_stream stream) {
 md_status md_build_cells(md_system *s, int32_t force, md_stream stream) {
   if (!s) return MD_ERR_INVALID_ARG;
   MD_CUDA(launch_bin(s->a, force ? 1 : 0, reinterpret_cast<cudaStream_t>(stream)));
+  s->bin_cond = true;
   if (force) {
-    s->binned = true;
+    s->binned = s->bin_all = true;
     s->listed = false;  // rows refer to the cell stages of the previous binning
     s->built = false;
   }
@@ -631,8 +638,14 @@ md_status md_build_cells(md_system *s, int32_t force, md_stream stream) {
 md_status md_build_nlist(md_system *s, int32_t force, md_stream stream) {
   if (!s) return MD_ERR_INVALID_ARG;
   if (!s->binned) return MD_ERR_STATE;
-  MD_CUDA(launch_nlist(s->a, s->tune[MD_KERNEL_NLIST], force ? 1 : 0,
-                       reinterpret_cast<cudaStream_t>(stream)));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (force ? !s->bin_all : !s->bin_cond) {
+    // particles moved since the last binning: bin them again first
+    MD_CUDA(launch_bin(s->a, force ? 1 : 0, st));
+    s->bin_cond = true;
+    if (force) s->bin_all = true;
+  }
+  MD_CUDA(launch_nlist(s->a, s->tune[MD_KERNEL_NLIST], force ? 1 : 0, st));
   if (force) s->listed = true;
   return MD_OK;
 }
@@ -657,6 +670,7 @@ md_status md_integrate(md_system *s, int32_t half, md_stream stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (half == 1) {
     MD_CUDA(launch_integrate1(s->a, st));
+    s->bin_all = s->bin_cond = false;
     s->step++;
   } else {
     MD_CUDA(launch_integrate2(s->a, st));
@@ -670,6 +684,7 @@ md_status md_step(md_system *s, int32_t want_virial, md_stream stream) {
   md_status e = prepare(s, st);
   if (e != MD_OK) return e;
   e = enqueue_step(s, want_virial ? 1 : 0, st);
+  s->bin_all = s->bin_cond = false;
   if (e == MD_OK) s->step++;
   return e;
 }
@@ -689,6 +704,7 @@ md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream st
   const int gsteps = s->p.graph_steps;
   const int64_t rows = period > 0 ? (s->step + n_steps) / period - s->step / period : 0;
   MD_CUDA(launch_run_begin(s->a, thermo_out, period, rows, st));
+  if (n_steps > 0) s->bin_all = s->bin_cond = false;
   int64_t left = n_steps;
   while (left > 0) {
     if (gsteps > 0 && left >= gsteps && (period == 0 || s->step % period == 0)) {
@@ -756,6 +772,10 @@ md_status md_autotune(md_system *s, int32_t n_samples, int32_t block_stride, md_
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   md_status e = prepare(s, st);
   if (e != MD_OK) return e;
+  if (!s->bin_all) {  // the timed builds need a current binning
+    MD_CUDA(launch_bin(s->a, 1, st));
+    s->bin_all = s->bin_cond = true;
+  }
   cudaEvent_t e0, e1;
   MD_CUDA(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return MD_ERR_CUDA; }

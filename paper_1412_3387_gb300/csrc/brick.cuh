@@ -47,6 +47,7 @@ namespace mdgb {
 constexpr int kStageCells = 64;
 constexpr float kFar = 1e30f;  // sentinel coordinate
 constexpr int kMaxBrickThreads = 512;
+constexpr int kStagePad = 8;  // slots past a stage that the list build may read (not use)
 
 // Stage layout of one brick (global array, built per binning; copied to
 // shared memory by the kernels).  640 bytes.
@@ -124,19 +125,26 @@ __device__ __forceinline__ float4 lds4(uint32_t addr) {
   return v;
 }
 
+__device__ __forceinline__ float lds1(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ void sts16(uint32_t addr, uint16_t v) {
   asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
 }
 
 // ---- the block's view of its shared memory ---------------------------------
 
-// [3] descriptors, [2][cap + 1] positions, ([2][cap + 1] velocities), then
-// the computing warps' scratch (list build).
+// [3] descriptors, [2][cap + 1 + pad] positions, ([2][cap + 1 + pad]
+// velocities), then scratch.  Slot 0 is the sentinel; the pad lets the list
+// build read whole blocks of candidates past the end of a stage.
 struct BrickSmem {
   unsigned char *base;
   int cap;
   bool vel;
-  __host__ __device__ static int pitch(int cap) { return cap + 1; }
+  __host__ __device__ static int pitch(int cap) { return cap + 1 + kStagePad; }
   __host__ __device__ static size_t desc_bytes() { return 3 * sizeof(BrickDesc); }
   __host__ __device__ static size_t stage_bytes(int cap, bool vel) {
     return (size_t)2 * pitch(cap) * sizeof(float4) * (vel ? 2 : 1);

@@ -184,9 +184,12 @@ __device__ __forceinline__ void place(const KArgs &a, int p, int32_t v) {
   }
 }
 
-// One warp per cell: order the cell's members by particle index.
+// One warp per cell: order the cell's members by their FP32 x offset from the
+// cell centre, ties by particle index.  At a build every member lies inside
+// its cell, so each run of x-adjacent cells is then sorted by x (the list
+// build searches windows in such runs).
 __device__ __forceinline__ void cell_sort_one(const KArgs &a, int64_t cell, int force,
-                                              int32_t *buf) {
+                                              int32_t *buf, float *bx) {
   const int lane = threadIdx.x & 31;
   const int r = a.chunk_rep[cell / kChunkCells];
   if (!rebuilding(a, r, force)) return;
@@ -200,12 +203,20 @@ __device__ __forceinline__ void cell_sort_one(const KArgs &a, int64_t cell, int 
     for (int k = lane; k < cnt; k += 32) place(a, start + k, idx[k]);
     return;
   }
-  for (int k = lane; k < cnt; k += 32) buf[k] = idx[k];
+  for (int k = lane; k < cnt; k += 32) {
+    const int32_t v = idx[k];
+    buf[k] = v;
+    bx[k] = a.oref[v].x;
+  }
   __syncwarp();
   for (int k = lane; k < cnt; k += 32) {
-    int32_t v = buf[k];
+    const int32_t v = buf[k];
+    const float x = bx[k];
     int rank = 0;
-    for (int m = 0; m < cnt; m++) rank += buf[m] < v;
+    for (int m = 0; m < cnt; m++) {
+      const float xm = bx[m];
+      rank += (xm < x || (xm == x && buf[m] < v)) ? 1 : 0;
+    }
     place(a, start + rank, v);
   }
   __syncwarp();
@@ -214,10 +225,11 @@ __device__ __forceinline__ void cell_sort_one(const KArgs &a, int64_t cell, int 
 __global__ void k_cell_sort(KArgs a, int force) {
   if (quiet(a, force)) return;
   __shared__ int32_t buf[8][kMaxCellSort];
+  __shared__ float bx[8][kMaxCellSort];
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; cell < a.n_cells;
        cell += warps)
-    cell_sort_one(a, cell, force, buf[threadIdx.x >> 5]);
+    cell_sort_one(a, cell, force, buf[threadIdx.x >> 5], bx[threadIdx.x >> 5]);
 }
 
 // One warp per brick: the stage layout of its 64 stage cells (first slot and

@@ -6,8 +6,11 @@
 // particle, the paper's threads per particle; the block size is the paper's
 // other tuning parameter).  A particle's candidates are the members of the
 // 27 cells around its cell: a 3 x 3 x 3 sub-block of the stage, i.e. nine
-// contiguous runs of slots.  The W lanes of a particle split every run into W
-// contiguous parts.  After each block of U candidates the lanes of a
+// contiguous runs of three x-adjacent cells.  Cells keep their members sorted
+// by x, so each run is sorted by x at a build: the particle binary-searches
+// the part of each run within its reach in x (given its y-z distance to the
+// run's row of cells) and skips runs out of reach.  The W lanes of a particle
+// split that window into W contiguous parts.  After each block of U candidates the lanes of a
 // particle take an exclusive prefix sum of their hit counts and write their
 // hits straight into the row, in the pair kernel's tile layout (brick.cuh);
 // rows are then padded with the sentinel up to their group's tile count.
@@ -34,6 +37,7 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
                                            int j) {
   constexpr int PB = 32 / WB;
   constexpr int U = 8;
+  static_assert(U <= kStagePad, "a block of candidates may read U - 1 slots past a stage");
   const int lane = threadIdx.x & 31;
   const int qq = lane / WB, sl = lane & (WB - 1);
   const int q = j * PB + qq;
@@ -65,10 +69,51 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
   // the nine runs of the particle's 3 x 3 x 3 stencil: stage cells
   // (hx .. hx + 2, hy + dy, hz + dz) for the home cell (hx + 1, hy + 1, hz + 1)
   const int c0 = (hs.s & 3) - 1 + 4 * (((hs.s >> 2) & 3) - 1) + 16 * ((hs.s >> 4) - 1);
+  // x-windows (staged bricks).  At a build every member lies inside its cell
+  // and members are sorted by x within a cell, so a run of three x-adjacent
+  // cells is sorted by x.  The particle's candidates in a run lie within
+  //   |x_j - x_i| <= sqrt(r_list^2 + band - rho^2),
+  // rho = its y-z distance to the run's row of cells; a run with rho^2 above
+  // r_list^2 + band holds none.  eps (far above the FP32 rounding of stage
+  // coordinates) keeps the windows conservative.
+  const float hy = rp.hf[1], hz = rp.hf[2];
+  const float eps = 1e-4f * fmaxf(rp.hf[0], fmaxf(hy, hz));
+  const float yb = oi.y - (float)(((hs.s >> 2) & 3) - 2) * hy;  // height above the home row's lower face
+  const float zb = oi.z - (float)((hs.s >> 4) - 2) * hz;
+  auto xs = [&](int slot) { return lds1(src.spos + 16u * (uint32_t)(slot + 1)); };
   int n = 0;  // row length so far (the same in the particle's WB lanes)
   for (int rr = 0; rr < 9; rr++) {
     const int s = c0 + 4 * (rr % 3) + 16 * (rr / 3);
-    const int rlo = d.off[s], len = d.off[s + 3] - rlo;
+    int rlo = d.off[s], len = d.off[s + 3] - rlo;
+    if (!DIRECT) {
+      const int dyi = rr % 3, dzi = rr / 3;
+      const float ry = fmaxf((dyi == 0 ? yb : dyi == 2 ? hy - yb : 0.f) - eps, 0.f);
+      const float rz = fmaxf((dzi == 0 ? zb : dzi == 2 ? hz - zb : 0.f) - eps, 0.f);
+      const float rem = hi2 - fmaf(ry, ry, rz * rz);
+      if (!(rem >= 0.f)) {
+        len = 0;
+      } else {
+        const float wx = sqrtf(rem) + eps, klo = oi.x - wx, khi = oi.x + wx;
+        // first slot with x >= klo, then first slot with x > khi
+        int b = rlo, m = len;
+        while (m > 0) {
+          const int h = m >> 1;
+          const bool go = xs(b + h) < klo;
+          b = go ? b + h + 1 : b;
+          m = go ? m - h - 1 : h;
+        }
+        int e = b;
+        m = rlo + len - b;
+        while (m > 0) {
+          const int h = m >> 1;
+          const bool go = xs(e + h) <= khi;
+          e = go ? e + h + 1 : e;
+          m = go ? m - h - 1 : h;
+        }
+        rlo = b;
+        len = e - b;
+      }
+    }
     // this lane's part of the run; all lanes take part in every run, and the
     // loop runs to the warp's longest part so that the warp-wide vote and the
     // shuffles below see every lane
@@ -78,11 +123,21 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
     const int wlen = (int)__reduce_max_sync(FULL, (unsigned)mylen);
     for (int x0 = 0; x0 < wlen; x0 += U) {
       float4 oju[U];
+      if (DIRECT) {
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        const int slot = beg + x0 + u;
-        const bool valid = x0 + u < mylen && slot != hs.slot;
-        oju[u] = src.pos(valid ? (uint32_t)(slot + 1) : 0u);
+        for (int u = 0; u < U; u++) {
+          const int slot = beg + x0 + u;
+          const bool valid = x0 + u < mylen && slot != hs.slot;
+          oju[u] = src.pos(valid ? (uint32_t)(slot + 1) : 0u);
+        }
+      } else {
+        // the whole block is read (up to U - 1 slots past the lane's part,
+        // still inside the padded stage) and the slots that are not
+        // candidates are masked out below; a lane whose part has ended reads
+        // slots 0 .. U - 1
+        const uint32_t base = x0 < mylen ? src.spos + (uint32_t)(beg + x0 + 1) * 16u : src.spos;
+#pragma unroll
+        for (int u = 0; u < U; u++) oju[u] = lds4(base + 16u * u);
       }
       bool band = false;
       unsigned m = 0u;  // bit u: candidate x0 + u is a neighbour
@@ -112,6 +167,12 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
             m |= (hit ? 1u : 0u) << u;
           }
         }
+      }
+      if (!DIRECT) {
+        // candidates only: slots of this lane's part, not the particle itself
+        m &= (1u << min(max(mylen - x0, 0), U)) - 1u;
+        const int so = hs.slot - (beg + x0);
+        if ((unsigned)so < (unsigned)U) m &= ~(1u << so);
       }
       // compact: this lane's hits follow those of the particle's lower lanes
       const int h = __popc(m);
@@ -155,7 +216,7 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
 // Persistent over bricks b = blockIdx + t G (replicas that do not rebuild are
 // skipped); warp w takes the brick's passes w, w + C, ...
 template <int WB>
-__global__ void __launch_bounds__(kMaxBrickThreads) k_nlist(KArgs a, int cap, int force) {
+__global__ void __launch_bounds__(kMaxBrickThreads, 1) k_nlist(KArgs a, int cap, int force) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int PB = 32 / WB;
   if (!force && !a.ds->rebuild_any) return;  // no replica rebuilds this step
