@@ -17,12 +17,14 @@
 // for any home particle i and stage particle j of its stencil.
 //
 // A persistent block walks bricks b, b + G, b + 2G, ... with two stage
-// buffers: while its warps compute brick t, the 16-byte asynchronous copies
-// (cp.async) of brick t + 1's stage are in flight; after a block barrier the
-// warps add the shifts, and a second barrier publishes the stage.  A brick's
-// descriptor (stage layout: first slot and cell-list start of each stage
-// cell, home cells) is built once per binning (k_brick_desc) and read with one
-// coalesced load two bricks ahead.
+// buffers: while its warps compute brick t, brick t + 1's stage is in flight
+// as one bulk copy (cp.async.bulk) per stage cell, issued by one warp and
+// counted on the buffer's mbarrier (transaction bytes).  After brick t the
+// warps wait for that barrier's phase (bounded: a timeout raises
+// kErrTimeout), add the shifts, and a block barrier publishes the stage.  A
+// brick's descriptor (stage layout: first slot and cell-list start of each
+// stage cell, home cells) is built once per binning (k_brick_desc) and read
+// with one coalesced load two bricks ahead.
 //
 // Stage slot 0 is a sentinel particle far away (its r^2 to anything
 // overflows to +inf, never inside a cut-off, and 0 * its offset is 0).  Row
@@ -104,14 +106,52 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// 16-byte copy global -> shared, both 16-byte aligned, through L2 only.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Arrives once on `bar` and adds `bytes` to the transactions its current
+// phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
                : "memory");
 }
 
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Waits for the phase of `bar` with the given parity to complete, for at most
+// about a second (2^31 SM clocks); false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// global -> shared, completing as transaction bytes on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Orders this thread's generic-proxy shared-memory accesses before later
+// async-proxy (bulk copy) writes to the same memory.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // Shared-memory accesses through 32-bit shared-window addresses: one 128-bit
@@ -137,15 +177,16 @@ __device__ __forceinline__ void sts16(uint32_t addr, uint16_t v) {
 
 // ---- the block's view of its shared memory ---------------------------------
 
-// [3] descriptors, [2][cap + 1 + pad] positions, ([2][cap + 1 + pad]
-// velocities), then scratch.  Slot 0 is the sentinel; the pad lets the list
-// build read whole blocks of candidates past the end of a stage.
+// [3] descriptors, [2] mbarriers (+ pad to 16 B), [2][cap + 1 + pad]
+// positions, ([2][cap + 1 + pad] velocities), then scratch.  Slot 0 is the
+// sentinel; the pad lets the list build read whole blocks of candidates past
+// the end of a stage.
 struct BrickSmem {
   unsigned char *base;
   int cap;
   bool vel;
   __host__ __device__ static int pitch(int cap) { return cap + 1 + kStagePad; }
-  __host__ __device__ static size_t desc_bytes() { return 3 * sizeof(BrickDesc); }
+  __host__ __device__ static size_t desc_bytes() { return 3 * sizeof(BrickDesc) + 16; }
   __host__ __device__ static size_t stage_bytes(int cap, bool vel) {
     return (size_t)2 * pitch(cap) * sizeof(float4) * (vel ? 2 : 1);
   }
@@ -154,6 +195,10 @@ struct BrickSmem {
   }
   __device__ __forceinline__ BrickDesc &desc(long long t) const {
     return reinterpret_cast<BrickDesc *>(base)[t % 3];
+  }
+  // the mbarrier counting the copies of the stage buffer of brick t
+  __device__ __forceinline__ uint64_t *bar(long long t) const {
+    return reinterpret_cast<uint64_t *>(base + 3 * sizeof(BrickDesc)) + (t & 1);
   }
   __device__ __forceinline__ float4 *pos(long long t) const {
     return reinterpret_cast<float4 *>(base + desc_bytes()) + (t & 1) * pitch(cap);
@@ -174,23 +219,40 @@ __device__ __forceinline__ void desc_fetch(const KArgs &a, long long b, BrickDes
   for (int k = threadIdx.x; k < (int)(sizeof(BrickDesc) / 16); k += blockDim.x) d[k] = __ldg(src + k);
 }
 
-// Issues the copies of a brick's stage (positions, and velocities if vel4 is
-// given): warp w takes stage cells w, w + C, ...; its lanes a cell's members.
+// Warp 0 issues the copies of a brick's stage (positions, and velocities if
+// vel4 is given) as one bulk copy per stage cell (lanes over cells), counted
+// on `bar`; a brick served from global memory only arrives.  The buffer's
+// previous readers and writers fenced and synchronised before this.
 __device__ __forceinline__ void stage_issue(const KArgs &a, const BrickDesc &d, float4 *pos,
-                                            float4 *vel4, int cap) {
-  if (d.off[64] > cap) return;  // direct brick
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, C = blockDim.x >> 5;
-  for (int s = warp; s < kStageCells; s += C) {
+                                            float4 *vel4, uint64_t *bar, int cap) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const bool staged = d.off[64] <= cap;
+  if (lane == 0)
+    mbar_arrive_expect_tx(bar, staged ? (uint32_t)d.off[64] * 16u * (vel4 ? 2u : 1u) : 0u);
+  __syncwarp();
+  if (!staged) return;
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const int s = lane + 32 * k;
     const int o = d.off[s], n = d.off[s + 1] - o, st = d.start[s];
-    for (int m = lane; m < n; m += 32) {
-      cp_async16(pos + 1 + o + m, a.pos4f + st + m);
-      if (vel4) cp_async16(vel4 + 1 + o + m, a.vel4f + st + m);
+    if (n > 0) {
+      bulk_g2s(pos + 1 + o, a.pos4f + st, 16u * (uint32_t)n, bar);
+      if (vel4) bulk_g2s(vel4 + 1 + o, a.vel4f + st, 16u * (uint32_t)n, bar);
     }
   }
 }
 
-// Adds the stage cells' shifts to their copied offsets (same split as
-// stage_issue); the caller has waited for the copies and synchronised.
+// Waits for brick t's stage copies (buffer t & 1, its (t >> 1)-th use); on
+// timeout raises kErrTimeout and returns false.
+__device__ __forceinline__ bool stage_wait(const KArgs &a, const BrickSmem &M, long long t) {
+  if (mbar_wait(M.bar(t), (uint32_t)((t >> 1) & 1))) return true;
+  if ((threadIdx.x & 31) == 0) set_error(a.ds, kErrTimeout);
+  return false;
+}
+
+// Adds the stage cells' shifts to their copied offsets (warp w takes stage
+// cells w, w + C, ...); the caller has waited for the copies.
 __device__ __forceinline__ void stage_shift_all(const KArgs &a, const BrickDesc &d, float4 *pos,
                                                 int cap) {
   if (d.off[64] > cap) return;

@@ -1,7 +1,8 @@
 // Neighbour-list build (Sec. 5.1, Fig. "nlist").
 //
 // Persistent kernel over brick stages (brick.cuh): while a block's warps work
-// on one brick, the next brick's stage is copied into shared memory.  A warp
+// on one brick, the next brick's stage is copied into shared memory (bulk
+// copies counted on an mbarrier; one block barrier per brick).  A warp
 // takes passes of P = 32 / W particles of the brick (W = 2^m <= 32 lanes per
 // particle, the paper's threads per particle; the block size is the paper's
 // other tuning parameter).  A particle's candidates are the members of the
@@ -241,20 +242,24 @@ __global__ void __launch_bounds__(kMaxBrickThreads, 1) k_nlist(KArgs a, int cap,
   if (bt >= a.n_bricks) return;
   long long b1 = next(bt + G);
   if (threadIdx.x < 2) M.pos(threadIdx.x)[0] = make_float4(kFar, kFar, kFar, 0.f);
+  if (threadIdx.x == 0) {
+    mbar_init(M.bar(0), 1);
+    mbar_init(M.bar(1), 1);
+  }
   desc_fetch(a, bt, M.desc(0));
   if (b1 < a.n_bricks) desc_fetch(a, b1, M.desc(1));
+  fence_proxy_async();
   __syncthreads();
-  stage_issue(a, M.desc(0), M.pos(0), nullptr, cap);
-  cp_async_wait_all();
-  __syncthreads();
+  stage_issue(a, M.desc(0), M.pos(0), nullptr, M.bar(0), cap);
+  bool ok = stage_wait(a, M, 0);
   stage_shift_all(a, M.desc(0), M.pos(0), cap);
-  __syncthreads();
+  if (!__syncthreads_and(ok)) return;
   constexpr int kDescWords = (int)(sizeof(BrickDesc) / 16);
   for (long long t = 0; bt < a.n_bricks; t++) {
     const bool has1 = b1 < a.n_bricks;
     const long long b2 = has1 ? next(b1 + G) : a.n_bricks;
     const bool has2 = b2 < a.n_bricks;
-    if (has1) stage_issue(a, M.desc(t + 1), M.pos(t + 1), nullptr, cap);
+    if (has1) stage_issue(a, M.desc(t + 1), M.pos(t + 1), nullptr, M.bar(t + 1), cap);
     // the descriptor two bricks ahead: loaded now, stored after the work
     // (40 words; a block has at least 32 threads, so two per thread)
     uint4 dv0 = make_uint4(0u, 0u, 0u, 0u), dv1 = dv0;
@@ -276,10 +281,12 @@ __global__ void __launch_bounds__(kMaxBrickThreads, 1) k_nlist(KArgs a, int cap,
       if (k0 < kDescWords) dst[k0] = dv0;
       if (k1 < kDescWords) dst[k1] = dv1;
     }
-    cp_async_wait_all();
-    __syncthreads();
+    // brick t + 1's stage: wait for its copies, add the shifts, publish (the
+    // barrier also frees brick t's buffer for brick t + 2's copies)
+    ok = !has1 || stage_wait(a, M, t + 1);
     if (has1) stage_shift_all(a, M.desc(t + 1), M.pos(t + 1), cap);
-    __syncthreads();
+    fence_proxy_async();
+    if (!__syncthreads_and(ok)) return;
     bt = b1;
     b1 = b2;
   }

@@ -370,7 +370,8 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
 }
 
 // Persistent over bricks b = blockIdx + t G.  Warp w takes the brick's row
-// groups w, w + C, ...; the next brick's stage copies run meanwhile.
+// groups w, w + C, ...; the next brick's stage copies run meanwhile.  One
+// block barrier per brick.
 template <int POT, int W, bool MIXED, bool ENERGY, bool ONE>
 __global__ void __launch_bounds__(kMaxBrickThreads) k_pair(KArgs a, int cap) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -385,20 +386,25 @@ __global__ void __launch_bounds__(kMaxBrickThreads) k_pair(KArgs a, int cap) {
     M.pos(threadIdx.x)[0] = make_float4(kFar, kFar, kFar, 0.f);
     if (VEL) M.vel4(threadIdx.x)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  if (threadIdx.x == 0) {
+    mbar_init(M.bar(0), 1);
+    mbar_init(M.bar(1), 1);
+  }
   desc_fetch(a, b0, M.desc(0));
   if (b0 + G < a.n_bricks) desc_fetch(a, b0 + G, M.desc(1));
+  fence_proxy_async();
   __syncthreads();
-  stage_issue(a, M.desc(0), M.pos(0), VEL ? M.vel4(0) : nullptr, cap);
-  cp_async_wait_all();
-  __syncthreads();
+  stage_issue(a, M.desc(0), M.pos(0), VEL ? M.vel4(0) : nullptr, M.bar(0), cap);
+  bool ok = stage_wait(a, M, 0);
   stage_shift_all(a, M.desc(0), M.pos(0), cap);
-  __syncthreads();
+  if (!__syncthreads_and(ok)) return;
   constexpr int kDescWords = (int)(sizeof(BrickDesc) / 16);
   for (long long t = 0;; t++) {
     const long long bt = b0 + t * G;
     if (bt >= a.n_bricks) break;
     const bool has1 = bt + G < a.n_bricks, has2 = bt + 2 * G < a.n_bricks;
-    if (has1) stage_issue(a, M.desc(t + 1), M.pos(t + 1), VEL ? M.vel4(t + 1) : nullptr, cap);
+    if (has1)
+      stage_issue(a, M.desc(t + 1), M.pos(t + 1), VEL ? M.vel4(t + 1) : nullptr, M.bar(t + 1), cap);
     // the descriptor two bricks ahead: loaded now, stored after the work
     // (40 words; a block has at least 32 threads, so two per thread)
     uint4 dv0 = make_uint4(0u, 0u, 0u, 0u), dv1 = dv0;
@@ -426,10 +432,12 @@ __global__ void __launch_bounds__(kMaxBrickThreads) k_pair(KArgs a, int cap) {
       if (k0 < kDescWords) dst[k0] = dv0;
       if (k1 < kDescWords) dst[k1] = dv1;
     }
-    cp_async_wait_all();
-    __syncthreads();  // brick t done everywhere; brick t + 1's copies have landed
+    // brick t + 1's stage: wait for its copies, add the shifts, publish (the
+    // barrier also frees brick t's buffer for brick t + 2's copies)
+    ok = !has1 || stage_wait(a, M, t + 1);
     if (has1) stage_shift_all(a, M.desc(t + 1), M.pos(t + 1), cap);
-    __syncthreads();
+    fence_proxy_async();
+    if (!__syncthreads_and(ok)) return;
   }
 }
 
