@@ -165,6 +165,31 @@ __device__ __forceinline__ float4 lds4(uint32_t addr) {
   return v;
 }
 
+// A staged particle as two packed FP32 pairs, (x, y) and (z, w).
+__device__ __forceinline__ void lds_pairs(uint32_t addr, uint64_t &xy, uint64_t &zw) {
+  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(xy), "=l"(zw) : "r"(addr) : "memory");
+}
+
+__device__ __forceinline__ uint64_t pack2(float x, float y) {
+  uint64_t v;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(x), "f"(y));
+  return v;
+}
+
+__device__ __forceinline__ float2 unpack2(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+
+// Packed FP32 subtraction (two IEEE round-to-nearest differences in one
+// instruction).
+__device__ __forceinline__ uint64_t sub_f32x2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 __device__ __forceinline__ float lds1(uint32_t addr) {
   float v;
   asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");

@@ -249,6 +249,12 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
     }
   }
 
+  // the mixed LJ block test: an entry with |r^2 - r_cut^2| within the band
+  // (with a little room for the rounding of the band's ends) sends the block
+  // through the FP64 re-test
+  const uint64_t oixy = pack2(oi.x, oi.y);
+  const float rc2f = a.rc2f, bthr = 1.001f * rp.band;
+
   // U entries at a time; the full blocks load the next block ahead without
   // bounds tests, the last T mod U tiles go one at a time (nu = 1)
   auto work = [&](const uint32_t *e, const int nu) {
@@ -257,17 +263,32 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
       // straight-line LJ: every entry is evaluated and masked (the sentinel's
       // r^2 is +inf); entries in the FP64 tie-break band are settled after
       // the group
-      bool band = false;
+      float bmin = 3.0e38f;  // smallest |r^2 - r_cut^2| of the block
 #pragma unroll
       for (int u = 0; u < nu; u++) {
-        const float4 oj = src.pos(e[u]);
-        const float dx = oi.x - oj.x, dy = oi.y - oj.y, dz = oi.z - oj.z;
+        float dx, dy, dz, ojw;
+        if (DIRECT) {
+          const float4 oj = src.pos(e[u]);
+          dx = oi.x - oj.x;
+          dy = oi.y - oj.y;
+          dz = oi.z - oj.z;
+          ojw = oj.w;
+        } else {
+          uint64_t xy, zw;
+          lds_pairs(src.spos + e[u] * 16u, xy, zw);
+          const float2 dxy = unpack2(sub_f32x2(oixy, xy));
+          const float2 ozw = unpack2(zw);
+          dx = dxy.x;
+          dy = dxy.y;
+          dz = oi.z - ozw.x;
+          ojw = ozw.y;
+        }
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         const bool in = r2 < mp.rc2_lo;
-        band |= (r2 >= mp.rc2_lo) & (r2 < mp.rc2_hi);
+        bmin = fminf(bmin, fabsf(r2 - rc2f));
         const LJCoeffF c = ONE ? mp.lj0
                                : reinterpret_cast<const LJCoeffF *>(a.coeff)[
-                                     mp.ti * a.ntypes + cell_type(__float_as_uint(oj.w))];
+                                     mp.ti * a.ntypes + cell_type(__float_as_uint(ojw))];
         const float r2i = __fdividef(1.0f, r2);
         const float r6 = r2i * r2i * r2i;
         const float fr = in ? r2i * r6 * (c.lj1 * r6 - c.lj2) : 0.f;
@@ -282,7 +303,7 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
           kw[3].add(0.5f * dy * fy); kw[4].add(0.5f * dy * fz); kw[5].add(0.5f * dz * fz);
         }
       }
-      if (__any_sync(FULL, band)) {
+      if (__any_sync(FULL, bmin <= bthr)) {
 #pragma unroll
         for (int u = 0; u < nu; u++) {
           const float4 oj = src.pos(e[u]);
