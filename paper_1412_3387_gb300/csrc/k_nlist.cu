@@ -51,6 +51,10 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
   const StageSrc<DIRECT> src{a, d, rp, smem_u32(spos), 0u};
   const float4 oi = src.pos((uint32_t)(hs.slot + 1));
   const float lo2 = a.rl2f - rp.band, hi2 = a.rl2f + rp.band;
+  // a block with some |r^2 - r_list^2| within the band (a little room for the
+  // rounding of the band's ends) goes through the FP64 re-test
+  const float bthr = 1.001f * rp.band;
+  const uint64_t oixy = pack2(oi.x, oi.y);
   const int max_nb = a.max_nb;
   // the pair kernel's row layout: groups of Pp = 32 / Wp particles, tiles of
   // Wp columns per particle; this lane owns RC = Wp / WB of the columns of its
@@ -123,13 +127,17 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
     const int mylen = active ? min(max(len - sl * part, 0), part) : 0;
     const int wlen = (int)__reduce_max_sync(FULL, (unsigned)mylen);
     for (int x0 = 0; x0 < wlen; x0 += U) {
-      float4 oju[U];
+      // r^2 of the block's candidates (the (x, y) separation as one packed
+      // FP32 pair difference)
+      float r2u[U];
       if (DIRECT) {
 #pragma unroll
         for (int u = 0; u < U; u++) {
           const int slot = beg + x0 + u;
           const bool valid = x0 + u < mylen && slot != hs.slot;
-          oju[u] = src.pos(valid ? (uint32_t)(slot + 1) : 0u);
+          const float4 oj = src.pos(valid ? (uint32_t)(slot + 1) : 0u);
+          const float dx = oi.x - oj.x, dy = oi.y - oj.y, dz = oi.z - oj.z;
+          r2u[u] = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
         }
       } else {
         // the whole block is read (up to U - 1 slots past the lane's part,
@@ -137,20 +145,24 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
         // candidates are masked out below; a lane whose part has ended reads
         // slots 0 .. U - 1
         const uint32_t base = x0 < mylen ? src.spos + (uint32_t)(beg + x0 + 1) * 16u : src.spos;
+        uint64_t xy[U], zw[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) oju[u] = lds4(base + 16u * u);
+        for (int u = 0; u < U; u++) lds_pairs(base + 16u * u, xy[u], zw[u]);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const float2 dxy = unpack2(sub_f32x2(oixy, xy[u]));
+          const float dz = oi.z - unpack2(zw[u]).x;
+          r2u[u] = fmaf(dz, dz, fmaf(dxy.y, dxy.y, dxy.x * dxy.x));
+        }
       }
-      bool band = false;
-      unsigned m = 0u;  // bit u: candidate x0 + u is a neighbour
+      float bmin = 3.0e38f;  // smallest |r^2 - r_list^2| of the block
+      unsigned m = 0u;       // bit u: candidate x0 + u is a neighbour
 #pragma unroll
       for (int u = 0; u < U; u++) {
-        const float4 oj = oju[u];
-        const float dx = oi.x - oj.x, dy = oi.y - oj.y, dz = oi.z - oj.z;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        band |= (r2 >= lo2) & (r2 < hi2);
-        m |= (r2 < lo2 ? 1u : 0u) << u;
+        bmin = fminf(bmin, fabsf(r2u[u] - a.rl2f));
+        m |= (r2u[u] < lo2 ? 1u : 0u) << u;
       }
-      if (__any_sync(FULL, band)) {
+      if (__any_sync(FULL, bmin <= bthr)) {
         // rare: decide the block's band candidates in FP64 with the oracle's
         // operation order
         const int32_t i = ident ? p : __ldg(a.cell_idx + p);
