@@ -359,11 +359,13 @@ def main():
         del sysm
         torch.cuda.empty_cache()
 
-        # launches in the timed region: per step integrate(1) + 8 binning
-        # (7 cell-list kernels + brick descriptors) + 2 sort + nlist + pair +
-        # integrate(2); 2 thermo kernels per thermo step.  The binning, sort
-        # and list kernels return at once on steps without a rebuild.
-        launches = args.steps * (1 + 8 + 2 + 1 + 1 + 1) + 2 * (args.steps // 100)
+        # launches in the timed region: per step integrate(1) (with the
+        # previous step's second half-kick folded in) + 8 binning (7 cell-list
+        # kernels + brick descriptors) + 2 sort + nlist + pair; per 100-step
+        # graph the closing half-kick integrate(2) and 2 thermo kernels.  The
+        # binning, sort and list kernels return at once on steps without a
+        # rebuild.
+        launches = args.steps * (1 + 8 + 2 + 1 + 1) + 3 * (args.steps // 100)
 
         forms = {"mixed": {"value": value, "ms_per_step": ms_per_step, "steps": args.steps}}
         if args.forms == "all":

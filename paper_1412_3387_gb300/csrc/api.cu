@@ -246,15 +246,19 @@ md_status make_plan(const md_params *p, Plan &pl) {
 template <class T>
 T *at(void *base, size_t off) { return reinterpret_cast<T *>(static_cast<char *>(base) + off); }
 
-md_status enqueue_step(md_system *s, int want_virial, cudaStream_t st) {
+// One step.  fold_in: the previous step left its second half-kick out, this
+// step's first half applies both.  close: apply this step's second half-kick
+// (else it is left to the next step; velocities then hold v(t + 1/2)).
+md_status enqueue_step(md_system *s, int want_virial, cudaStream_t st, bool fold_in = false,
+                       bool close = true) {
   const KArgs &a = s->a;
-  MD_CUDA(launch_integrate1(a, st));
+  MD_CUDA(launch_integrate1(a, st, fold_in));
   MD_CUDA(launch_bin(a, 0, st));
   if (s->p.sort_period > 0) MD_CUDA(launch_sort(a, 0, st));
   MD_CUDA(launch_nlist(a, s->tune[MD_KERNEL_NLIST], 0, st));
   MD_CUDA(launch_pair(a, s->tune[MD_KERNEL_PAIR], want_virial, st));
   if (s->n_bonds > 0) MD_CUDA(launch_bonds(a, want_virial, st));
-  MD_CUDA(launch_integrate2(a, st));
+  if (close) MD_CUDA(launch_integrate2(a, st));
   return MD_OK;
 }
 
@@ -713,9 +717,14 @@ md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream st
         cudaGraph_t g = nullptr;
         MD_CUDA(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
         md_status ce = MD_OK;
+        // inside the graph a step's second half-kick is folded into the next
+        // step's first half, except on thermo steps (they need full-step
+        // velocities) and the last step (the graph ends in a full step)
         for (int l = 0; l < gsteps && ce == MD_OK; l++) {
           const int th = period > 0 && (l + 1) % period == 0;
-          ce = enqueue_step(s, th, s->cap);
+          const bool prev_open = l > 0 && !(period > 0 && l % period == 0);
+          const bool close = th || l == gsteps - 1;
+          ce = enqueue_step(s, th, s->cap, prev_open, close);
           if (ce == MD_OK && th && launch_thermo(s->a, nullptr, 1, s->cap) != cudaSuccess) ce = MD_ERR_CUDA;
         }
         cudaError_t ee = cudaStreamEndCapture(s->cap, &g);

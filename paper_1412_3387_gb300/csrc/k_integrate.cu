@@ -77,7 +77,10 @@ __device__ __forceinline__ void kick_drift(double &x, double &v, int &img, doubl
 // positions and the rebuild check of Sec. 4.2 (a particle moved more than half
 // the buffer since the last build -> raise the replica's flag).  The last
 // block to finish advances the step counter and decides the sorts.
-__global__ void k_integrate1(KArgs a) {
+// hk = dt / (2m); or dt / m when the previous step's second half-kick was
+// left out (inside a run): v(t - 1/2) -> v(t + 1/2) = v(t - 1/2) + dt F(t) / m,
+// the same velocity-Verlet step written as one kick.
+__global__ void k_integrate1(KArgs a, double hk) {
   __shared__ int is_last;
   const int64_t t = a.ds->step;
   const int par = (int)((t + 1) & 1);
@@ -90,7 +93,6 @@ __global__ void k_integrate1(KArgs a) {
     const double3 f = ld_force3(a, i);
     int4 img = a.image[i];
     const int4 img0 = img;
-    const double hk = a.half_dt_m;
     kick_drift(x.x, v.x, img.x, f.x, hk, a.dt, rp.L[0]);
     kick_drift(x.y, v.y, img.y, f.y, hk, a.dt, rp.L[1]);
     kick_drift(x.z, v.z, img.z, f.z, hk, a.dt, rp.L[2]);
@@ -391,9 +393,10 @@ __global__ void k_philox(const uint32_t *in, uint32_t *out, int64_t n) {
 
 }  // namespace
 
-cudaError_t launch_integrate1(const KArgs &a, cudaStream_t st) {
+cudaError_t launch_integrate1(const KArgs &a, cudaStream_t st, bool fold_kick) {
   // the step counter must advance even for an empty system
-  k_integrate1<<<blocks_for(a.n > 0 ? a.n : 1, 256), 256, 0, st>>>(a);
+  k_integrate1<<<blocks_for(a.n > 0 ? a.n : 1, 256), 256, 0, st>>>(
+      a, fold_kick ? 2.0 * a.half_dt_m : a.half_dt_m);
   return cudaGetLastError();
 }
 

@@ -245,7 +245,8 @@ __device__ __forceinline__ uint32_t dpd_word(int32_t ti, int32_t tj, uint64_t st
 // ---- launch wrappers (defined in the k_*.cu files) ------------------------
 struct Launch { int block; int w; };
 
-cudaError_t launch_integrate1(const KArgs &a, cudaStream_t st);
+// fold_kick: also apply the previous step's second half-kick (it was left out)
+cudaError_t launch_integrate1(const KArgs &a, cudaStream_t st, bool fold_kick = false);
 cudaError_t launch_integrate2(const KArgs &a, cudaStream_t st);
 cudaError_t launch_bin(const KArgs &a, int force, cudaStream_t st);
 cudaError_t launch_sort(const KArgs &a, int force, cudaStream_t st);
