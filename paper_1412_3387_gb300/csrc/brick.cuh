@@ -148,11 +148,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       : "memory");
 }
 
-// Asks L2 to fetch `bytes` (a multiple of 16) from a 16-byte aligned address.
-__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 // Orders this thread's generic-proxy shared-memory accesses before later
 // async-proxy (bulk copy) writes to the same memory.
 __device__ __forceinline__ void fence_proxy_async() {

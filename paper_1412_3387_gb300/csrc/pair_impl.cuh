@@ -327,12 +327,6 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
     }
   };
   const int Tm = T & ~(U - 1);
-  // the group's rows are one contiguous region: one bulk request brings it
-  // to L2 while the first block is loaded
-  if (lane == 0 && T > U) {
-    const uint16_t *base = a.nl + (size_t)pg * (size_t)a.max_nb;
-    prefetch_l2(base, ((uint32_t)(T * stride) * 2u + 15u) & ~15u);
-  }
   uint32_t nxt[U];
 #pragma unroll
   for (int u = 0; u < U; u++) nxt[u] = u < T ? (uint32_t)__ldcs(rows + u * stride) : 0u;
@@ -351,15 +345,11 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
     }
     work(e, U);
   }
-  // the last T mod U tiles, already loaded, one at a time (a rolled loop:
-  // one copy of the entry code, the loaded entries shift down)
+  // the last T mod U tiles, already loaded, one at a time
   const int rem = T - Tm;
-#pragma unroll 1
-  for (int k = 0; k < rem; k++) {
-    work(&nxt[0], 1);
 #pragma unroll
-    for (int u = 0; u + 1 < U; u++) nxt[u] = nxt[u + 1];
-  }
+  for (int u = 0; u < U; u++)
+    if (u < rem) work(&nxt[u], 1);
 
   // combine the W partial sums of each particle (intra-warp reduction)
   if (MIXED) {
@@ -398,21 +388,6 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
       }
     }
   }
-}
-
-// The rare variants (a brick served from global memory; the brick's last,
-// partial group) run out of line, so that the hot kernel body (the full
-// groups) stays small in the instruction cache.
-template <int POT, int W, bool MIXED, bool ENERGY, bool ONE>
-__device__ __noinline__ void pair_group_direct(const KArgs &a, const BrickDesc &d, int j,
-                                               uint64_t step) {
-  pair_group<POT, W, MIXED, ENERGY, ONE, true, false>(a, d, nullptr, nullptr, j, step);
-}
-template <int POT, int W, bool MIXED, bool ENERGY, bool ONE>
-__device__ __noinline__ void pair_group_partial(const KArgs &a, const BrickDesc &d,
-                                                const float4 *spos, const float4 *svel, int j,
-                                                uint64_t step) {
-  pair_group<POT, W, MIXED, ENERGY, ONE, false, false>(a, d, spos, svel, j, step);
 }
 
 // Persistent over bricks b = blockIdx + t G.  Warp w takes the brick's row
@@ -463,13 +438,14 @@ __global__ void __launch_bounds__(kMaxBrickThreads) k_pair(KArgs a, int cap) {
     const BrickDesc &d = M.desc(t);
     const int ng = (d.nhome + P - 1) / P;
     if (d.off[64] > cap) {
-      for (int j = warp; j < ng; j += C) pair_group_direct<POT, W, MIXED, ENERGY, ONE>(a, d, j, step);
+      for (int j = warp; j < ng; j += C)
+        pair_group<POT, W, MIXED, ENERGY, ONE, true, false>(a, d, M.pos(t), M.vel4(t), j, step);
     } else {
       for (int j = warp; j < ng; j += C) {
         if ((j + 1) * P <= d.nhome)
           pair_group<POT, W, MIXED, ENERGY, ONE, false, true>(a, d, M.pos(t), M.vel4(t), j, step);
         else
-          pair_group_partial<POT, W, MIXED, ENERGY, ONE>(a, d, M.pos(t), M.vel4(t), j, step);
+          pair_group<POT, W, MIXED, ENERGY, ONE, false, false>(a, d, M.pos(t), M.vel4(t), j, step);
       }
     }
     if (has2) {
