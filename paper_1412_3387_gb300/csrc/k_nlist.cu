@@ -233,6 +233,10 @@ __global__ void __launch_bounds__(kMaxBrickThreads, 1) k_nlist(KArgs a, int cap,
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int PB = 32 / WB;
   if (!force && !a.ds->rebuild_any) return;  // no replica rebuilds this step
+  // After a non-finite position or an over-full cell the step's results are
+  // invalid (the host sees the error); skip the build: non-finite positions
+  // all bin into one cell, whose stage the build would scan quadratically.
+  if (__ldcg(&a.ds->error) & (kErrNonfinite | kErrCellOverflow)) return;
   const long long step = a.ds->step;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     // the pair kernel runs after this launch has finished (stream order)
