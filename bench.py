@@ -176,6 +176,23 @@ def dist_setup(args):
     return rank, world, local, pg
 
 
+def slowest_rank_time(elapsed, dist, device):
+    """Length of the timed region: the slowest rank's (max over ranks; every
+    rank gets it)."""
+    if not dist:
+        return elapsed
+    import torch
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(n_per_rank, steps, world, t_max):
+    """Particle-steps per second of the whole job: every rank advanced its own
+    n_per_rank particles by `steps` steps within t_max."""
+    return n_per_rank * steps * world / t_max
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU FP64 oracle, as it stands, on the host cores."""
     if rank != 0:
@@ -286,12 +303,8 @@ def main():
                 dist.barrier()
         sysm.check_error()
         builds = sysm.info()["n_builds"] - builds0
-        t_max = elapsed
-        if dist:
-            tt = torch.tensor([elapsed], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_max = float(tt.item())
-        value = args.n * args.steps * world / t_max
+        t_max = slowest_rank_time(elapsed, dist, dev)
+        value = whole_job_rate(args.n, args.steps, world, t_max)
         ms_per_step = 1e3 * t_max / args.steps
 
         if args.profile_pass:
