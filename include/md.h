@@ -50,7 +50,9 @@ typedef enum {
     MD_ERR_NONFINITE = 6,            /* non-finite position after integration */
     MD_ERR_CELL_OVERFLOW = 7,        /* a cell held more particles than can be ordered */
     MD_ERR_STATE = 8,                /* call not valid in the current state */
-    MD_ERR_TIMEOUT = 9               /* a kernel's internal wait gave up (an internal error) */
+    MD_ERR_TIMEOUT = 9               /* a kernel's wait for its own shared-memory copies gave
+                                        up after about a second (an internal error); the
+                                        kernel returned early */
 } md_status;
 
 typedef enum { MD_FP64 = 0, MD_MIXED = 1 } md_precision;
@@ -187,9 +189,15 @@ md_status md_reduce_thermo(md_system *s, double *dev_out, md_stream stream);
 
 /* Runs n_steps full steps; segments of graph_steps steps replay one captured
  * CUDA graph (captured on first use, re-captured after md_autotune or
- * md_set_tuning).  If thermo_out (DEVICE, [n_steps / thermo_period][R][8]) is
+ * md_set_tuning).  Inside a graph each step's second half-kick is folded into
+ * the next step's first (velocities hold v(t + 1/2) in between); thermo steps
+ * and the last step of every graph end with the plain second half-kick, so
+ * the velocities are full-step ones wherever thermo reads them and when the
+ * call returns.  If thermo_out (DEVICE, [n_steps / thermo_period][R][8]) is
  * not NULL, a thermo row is written after every step t with
- * t % thermo_period == 0, in order. */
+ * t % thermo_period == 0, in order.  While the device error word holds a
+ * non-finite position or an over-full cell, list builds are skipped (the
+ * steps' results are invalid; md_poll_error reports the error). */
 md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream stream);
 
 /* Autotuner (Sec. 5.2): for the pair and neighbour-list kernels, times every
