@@ -420,6 +420,23 @@ def test_nlist_overflow_is_reported():
     assert code == 4 and detail > 32
 
 
+def test_nonfinite_position_is_reported_and_stops_list_builds():
+    """A NaN coordinate is flagged by the first integration half (with the
+    particle's index); later list builds are skipped, so a run of graphs over
+    the failed state still ends at once."""
+    import time
+    st = lj_state(n=4000)
+    st.pos[123, 0] = np.nan
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, graph_steps=100, thermo_period=100,
+                    sort_period=1)
+    s.prepare()
+    t0 = time.perf_counter()
+    s.run(200)
+    code, detail = s.poll_error()
+    assert time.perf_counter() - t0 < 30.0
+    assert code == 6 and detail == 123, (code, detail)
+
+
 @pytest.mark.parametrize("prec", ("fp64", "mixed"))
 def test_nve_energy_drift(prec):
     """Shifted-energy drift over 1e4 steps at dt = 0.005 after 1000
