@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -84,7 +85,8 @@ class Clocks:
 
     def __init__(self, device_index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples in a temporary file; the summary goes into the JSON line
+        self.path = os.path.join(tempfile.gettempdir(), f"md_bench_clocks_{os.getpid()}.csv")
         self.idx = device_index
 
     def __enter__(self):
