@@ -206,7 +206,10 @@ __device__ __forceinline__ void cell_sort_one(const KArgs &a, int64_t cell, int 
   for (int k = lane; k < cnt; k += 32) {
     const int32_t v = idx[k];
     buf[k] = v;
-    bx[k] = a.oref[v].x;
+    // a non-finite offset (flagged elsewhere) ranks as +inf: the order stays
+    // strict, so every member gets its own place
+    const float x = a.oref[v].x;
+    bx[k] = x == x ? x : INFINITY;
   }
   __syncwarp();
   for (int k = lane; k < cnt; k += 32) {
