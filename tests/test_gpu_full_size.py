@@ -21,6 +21,7 @@ import pytest
 
 import oracle
 from paper_1412_3387_gb300 import inputs
+from local_ref import local_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -41,35 +42,6 @@ def _built():
     from paper_1412_3387_gb300 import build
     build.build()
     oracle.build()
-
-
-def local_reference(pos, L, samples):
-    """For each sampled particle: its oracle row (global indices, ascending)
-    and oracle force, from the particle and the members of its 27 cells."""
-    r_list = R_CUT + R_SKIN
-    nc = oracle.cells_per_dim(L, r_list)
-    cc = oracle.cell_coords(pos, L, [nc] * 3).astype(np.int64)
-    cid = cc[:, 0] + nc * (cc[:, 1] + nc * cc[:, 2])
-    order = np.argsort(cid, kind="stable")
-    starts = np.searchsorted(cid[order], np.arange(nc ** 3 + 1))
-    rows, forces, absf = [], [], []
-    for i in samples:
-        cx, cy, cz = cc[i]
-        parts = []
-        for dz in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                for dx in (-1, 0, 1):
-                    c = ((cx + dx) % nc) + nc * (((cy + dy) % nc) + nc * ((cz + dz) % nc))
-                    parts.append(order[starts[c]:starts[c + 1]])
-        idx = np.unique(np.concatenate(parts))  # small boxes repeat cells
-        loc = int(np.searchsorted(idx, i))
-        sub = pos[idx]
-        cnt, rw = oracle.neighbors(sub, L, r_list, max_nb=256, method="brute")
-        rows.append(np.sort(idx[rw[loc, :cnt[loc]]]))
-        f, _, af = oracle.lj_forces(sub, L, R_CUT)
-        forces.append(f[loc])
-        absf.append(af[loc])
-    return rows, np.array(forces), np.array(absf)
 
 
 def gpu_rows(s, samples):
@@ -107,7 +79,7 @@ def test_headline_fluid_sampled_rows_and_forces():
                           [np.argsort(pos[:, k])[-4:] for k in range(3)])
     samples = np.unique(np.concatenate([rng.choice(N, 1500, replace=False), edge]))
 
-    rows_ref, f_ref, absf = local_reference(pos, L, samples)
+    rows_ref, f_ref, absf = local_reference(pos, L, samples, R_CUT, R_SKIN)
     rows_mixed = gpu_rows(s, samples)
     for k, i in enumerate(samples):
         assert np.array_equal(rows_mixed[k], rows_ref[k]), int(i)

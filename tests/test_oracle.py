@@ -403,3 +403,24 @@ def test_sfc_order_is_permutation_walking_adjacent_bricks():
     b = bricks[::8]
     assert np.all(np.abs(np.diff(b, axis=0)).sum(1) == 1)
     assert b[0].tolist() == [0, 0, 0]
+
+
+def test_local_neighbourhood_answers_equal_whole_system_ones():
+    """The per-particle oracle answers the headline-size GPU test uses (the
+    particle and its 27 cells) equal the whole-system oracle answers, for
+    random particles and the ones next to each face of the box."""
+    from local_ref import local_reference
+    st = inputs.lj_fluid(32000, 0.8442, 1.2, seed=12345, jitter=0.05)
+    pos, L = st.pos, st.box[0, 0]
+    rng = np.random.default_rng(3)
+    edge = np.concatenate([np.argsort(pos[:, k])[:3] for k in range(3)] +
+                          [np.argsort(pos[:, k])[-3:] for k in range(3)])
+    samples = np.unique(np.concatenate([rng.choice(st.n, 100, replace=False), edge]))
+    rows, f, absf = local_reference(pos, L, samples, 2.5, 0.4)
+    cb, rb = oracle.neighbors(pos, L, 2.9, max_nb=256, method="cells")
+    fr, _, afr = oracle.lj_forces(pos, L, 2.5, nlist=(cb, rb))
+    for k, i in enumerate(samples):
+        assert np.array_equal(rows[k], np.sort(rb[i, :cb[i]])), int(i)
+        d = np.linalg.norm(f[k, :3] - fr[i, :3])
+        assert d <= 1e-12 * max(np.linalg.norm(fr[i, :3]), 1e-2 * afr[i]), int(i)
+    assert np.allclose(absf, afr[samples], rtol=1e-12)
