@@ -16,13 +16,16 @@
  *   - Calls taking a stream only enqueue work on it and return without
  *     synchronising, unless stated otherwise.  Argument errors are reported
  *     immediately by the return code.  Errors found on the device (neighbour
- *     row overflow, non-finite force) are recorded in a device error word
- *     that md_poll_error() reads.
+ *     row overflow, a non-finite position, an over-full cell, a force
+ *     evaluation on a list that does not match the current binning, a timed-
+ *     out internal wait) are recorded in a device error word that
+ *     md_poll_error() reads.
  *   - The library never allocates device memory: the caller passes one
  *     workspace buffer sized by md_workspace_size().  The system handle itself
  *     lives in host memory owned by the library (md_destroy_system frees it).
- *   - Indices are int32: at most 134,217,728 particles per system (neighbour
- *     entries spend 5 of their 32 bits on the periodic image code).
+ *   - Indices are int32: at most 134,217,728 (2^27) particles per system.
+ *     Neighbour-list entries are 16-bit slots of a brick's shared-memory
+ *     stage, not particle indices (md_get_nlist decodes them).
  *   - Units are LJ / DPD reduced units, k_B = 1.
  */
 #ifndef MD_GB300_H
@@ -115,8 +118,11 @@ const char *md_status_string(md_status s);
 md_status md_workspace_size(const md_params *p, size_t *bytes);
 
 /* Creates a system over caller-owned particle arrays and workspace (both must
- * stay valid until md_destroy_system).  Builds the per-replica cell grids and
- * space-filling-curve cell order on the host, uploads them, and binds `parts`.
+ * stay valid until md_destroy_system).  Sec. 4.1: the single-GPU code path
+ * keeps all simulation data on the device and transfers nothing significant
+ * between host and device while it runs; the host only plans and launches.
+ * Builds the per-replica cell grids and space-filling-curve cell order on the
+ * host, uploads them, and binds `parts`.
  * Enqueues initialisation on `stream`; does not build the neighbour list.
  * Errors: MD_ERR_INVALID_ARG, MD_ERR_CELL_GRID, MD_ERR_WORKSPACE_TOO_SMALL,
  * MD_ERR_CUDA. */
@@ -124,7 +130,9 @@ md_status md_create_system(const md_params *p, const md_particles *parts,
                            void *workspace, size_t ws_bytes, md_stream stream,
                            md_system **out);
 
-/* Frees the host handle and any captured graph; the caller frees its memory. */
+/* Frees the host handle and any captured graph; the caller frees its memory.
+ * Not in the paper (resource handling of this interface).  Errors:
+ * MD_ERR_INVALID_ARG for a NULL handle. */
 md_status md_destroy_system(md_system *s);
 
 /* Harmonic bonds V = K/2 (r - r0)^2 between unordered pairs of particle IDs
@@ -135,9 +143,14 @@ md_status md_destroy_system(md_system *s);
 md_status md_set_bonds(md_system *s, const int32_t *bond_tags, int64_t n_bonds,
                        double K, double r0, md_stream stream);
 
-/* Space-filling-curve sort: reorders every caller particle array so that
- * particles follow the Hilbert order of their cells, then the binning's
- * order inside each cell (by x offset, then index).
+/* Space-filling-curve sort (Sec. 4.3.1: the particle arrays, positions,
+ * velocities and the rest, are reordered together, infrequently, at list
+ * rebuilds; the choice of a Hilbert curve over bricks of 2 x 2 x 2 cells is
+ * this library's): reorders every caller particle array into the cell list's
+ * order, i.e. bricks along the Hilbert curve, then the binning's order inside
+ * each brick (cells x first, then y, then z; in a cell by x offset from the
+ * cell centre, then index).  Errors: MD_ERR_INVALID_ARG, MD_ERR_STATE (no
+ * binning yet), MD_ERR_CUDA.
  * force = 0: only replicas that rebuild now and whose last sort is
  * >= sort_period steps old.  Requires md_build_cells to have binned the
  * current positions (it sorts by that binning). */
@@ -170,7 +183,12 @@ md_status md_build_nlist(md_system *s, int32_t force, md_stream stream);
  * Overwrites the force array. */
 md_status md_compute_pair(md_system *s, int32_t want_virial, md_stream stream);
 
-/* Adds harmonic-bond forces (md_set_bonds) to the force array. */
+/* Adds harmonic-bond forces (md_set_bonds) to the force array: each particle
+ * sums V = K/2 (r - r0)^2 over its own bonds (Sec. 3 lists harmonic bonds;
+ * Sec. 4.3.4: a bond is an unordered pair of particle IDs, so the partner is
+ * found through the tag table after any sort).  Per-particle energy gets half
+ * of each bond's V and the virial half of r f when want_virial = 1.  No-op
+ * without bonds.  Errors: MD_ERR_INVALID_ARG, MD_ERR_CUDA. */
 md_status md_compute_bonds(md_system *s, int32_t want_virial, md_stream stream);
 
 /* Velocity Verlet (Sec. 3).  half = 1: v += dt/2 F/m, x += dt v, wrap into the
@@ -224,9 +242,13 @@ md_status md_get_tuning(md_system *s, int32_t kernel, int32_t *block, int32_t *w
 md_status md_set_step(md_system *s, int64_t step, md_stream stream);
 md_status md_get_step(md_system *s, int64_t *step); /* synchronises */
 
-/* Synchronises the system's work and reads the device error word.  Returns
- * MD_OK or the first recorded error; *detail gets the required max_nb for
- * MD_ERR_NLIST_OVERFLOW, the particle index for MD_ERR_NONFINITE. */
+/* Synchronises the system's work and reads the device error word.  Not in
+ * the paper (error reporting of this interface).  Returns MD_OK or the first
+ * recorded error, in this order of precedence: MD_ERR_NLIST_OVERFLOW
+ * (*detail = the max_nb needed), MD_ERR_NONFINITE (*detail = the index of a
+ * particle with a non-finite position), MD_ERR_CELL_OVERFLOW, MD_ERR_STATE (a
+ * force evaluation found its replica's list stale and computed nothing),
+ * MD_ERR_TIMEOUT.  The word is not cleared.  detail may be NULL. */
 md_status md_poll_error(md_system *s, int64_t *detail);
 
 /* --- inspection (tests, diagnostics) ------------------------------------ */
@@ -261,16 +283,18 @@ md_status md_philox4x32_10(const uint32_t *dev_in, uint32_t *dev_out, int64_t n,
  * cannot allocate device memory at all (a plugin whose host program owns every
  * device allocation, a real-time loop that cannot afford cudaMalloc's implicit
  * synchronisation): it computes FP64 LJ 12-6 forces of ONE periodic system
- * without a workspace, binning the particles into cells of width >= r_cut and
- * summing every pair within r_cut over the 27 surrounding cells.
- *   dev_pos    DEVICE double [n][4] (x, y, z in [0, box), w ignored), 16-B aligned
+ * without a workspace, binning the particles into cells of width at least
+ * r_cut (1 + 1e-12) and summing every pair within r_cut over the 27
+ * surrounding cells (minimum image).
+ *   dev_pos    DEVICE double [n][4] (x, y, z; w ignored), 16-B aligned; any
+ *              finite coordinates (each is wrapped into [0, box) for binning)
  *   box        HOST double [3] edge lengths
  *   dev_force  DEVICE double [n][4] output: F, per-particle energy (half of each
  *              pair's unshifted V)
  * Scratch: a 4 MiB array in the library's device memory (1,048,576 int32),
  * reserved on every device the library is used on, until the process exits.
  * A call needs 3 n + 2 n_cells of them, n_cells = product over the edges of
- * min(floor(box / r_cut), 1024); larger systems get MD_ERR_WORKSPACE_TOO_SMALL
+ * min(floor(box / (r_cut (1 + 1e-12))), 1024); larger systems get MD_ERR_WORKSPACE_TOO_SMALL
  * before any launch.  Boxes under 3 cells per edge: MD_ERR_CELL_GRID.
  * The first call on a device looks up the array's device address (with that
  * device current): make that first call before any stream capture.  Calls use

@@ -494,15 +494,21 @@ uint64_t orc_hilbert3(uint32_t x, uint32_t y, uint32_t z, int32_t bits) {
     return h;
 }
 
-typedef struct { uint64_t key; float xo; int64_t idx; } keyidx_t;
+typedef struct { uint64_t key; int64_t idx; } keyidx_t;
 
 static int cmp_keyidx(const void *a, const void *b) {
     const keyidx_t *x = a, *y = b;
     if (x->key != y->key) return x->key < y->key ? -1 : 1;
-    if (x->xo != y->xo) return x->xo < y->xo ? -1 : 1;
     return (x->idx > y->idx) - (x->idx < y->idx);
 }
 
+/* Space-filling-curve order (Sec. 4.3.1 reorders all particle arrays
+ * together, at list rebuilds; the curve, a 3-D Hilbert curve, is the
+ * benchmark configuration's choice, not the paper's): the key of a particle is the
+ * Hilbert index of the brick of 2 x 2 x 2 cells holding its cell, on a grid
+ * of ceil(nc / 2) bricks per edge; particles with equal keys keep their index
+ * order.  Nothing finer is fixed by the method: the order of the cells of a
+ * brick and of the particles of a cell is left to the implementation. */
 void orc_sfc_order(int64_t n, const double *pos, const double *L, double r_list,
                    int32_t *order) {
     int32_t nc[3];
@@ -512,24 +518,14 @@ void orc_sfc_order(int64_t n, const double *pos, const double *L, double r_list,
         if (nc[k] == 0) nc[k] = 1;
         if (nc[k] > nmax) nmax = nc[k];
     }
-    /* the curve runs over bricks of 2 x 2 x 2 cells (ceil(nc / 2) per edge);
-     * inside a brick the cells go x first, then y, then z */
     int32_t bmax = (nmax + 1) / 2;
-    int32_t bits = 1;
+    int32_t bits = 1; /* bits >= 1 even for a single brick per edge */
     while ((1 << bits) < bmax) bits++;
-    /* bits >= 1 even for a single brick per edge */
     keyidx_t *ki = malloc(sizeof(keyidx_t) * (size_t)(n > 0 ? n : 1));
     for (int64_t i = 0; i < n; i++) {
         uint32_t c[3];
         for (int k = 0; k < 3; k++) c[k] = (uint32_t)cell_of(pos[4 * i + k], nc[k], L[k]);
-        const uint64_t brick = orc_hilbert3(c[0] >> 1, c[1] >> 1, c[2] >> 1, bits);
-        ki[i].key = brick * 8u + (c[0] & 1u) + 2u * (c[1] & 1u) + 4u * (c[2] & 1u);
-        /* inside a cell: by the x offset from the cell centre (c + 1/2) h,
-         * minimum image, rounded to FP32; then by index */
-        const double h = L[0] / nc[0];
-        double d = pos[4 * i] - fma((double)c[0], h, 0.5 * h);
-        d -= L[0] * rint(d / L[0]);
-        ki[i].xo = (float)d;
+        ki[i].key = orc_hilbert3(c[0] >> 1, c[1] >> 1, c[2] >> 1, bits);
         ki[i].idx = i;
     }
     qsort(ki, (size_t)n, sizeof(keyidx_t), cmp_keyidx);

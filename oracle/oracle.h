@@ -128,10 +128,11 @@ void orc_thermo(int64_t n, const double *vel, const double *force,
  * 2004: axes-to-transpose, then bit interleave). */
 uint64_t orc_hilbert3(uint32_t x, uint32_t y, uint32_t z, int32_t bits);
 
-/* Space-filling-curve order: particles ordered by the Hilbert index of the
- * brick of 2 x 2 x 2 cells holding their cell (cell list of minimum width
- * r_list), then by the cell's place in the brick (x, then y, then z); inside
- * a cell by the x offset from the cell centre (FP32), then by index. */
+/* Space-filling-curve order (Sec. 4.3.1: all particle arrays reordered
+ * together at list rebuilds; the Hilbert curve is the benchmark
+ * configuration's choice): particles ordered by the Hilbert index of the brick of 2 x 2 x 2
+ * cells (cell list of minimum width r_list) holding their cell, ties by
+ * index.  The order inside a brick is not part of the method. */
 void orc_sfc_order(int64_t n, const double *pos, const double *L, double r_list,
                    int32_t *order);
 

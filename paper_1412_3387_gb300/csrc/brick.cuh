@@ -276,6 +276,20 @@ __device__ __forceinline__ bool stage_wait(const KArgs &a, const BrickSmem &M, l
   return false;
 }
 
+// Leaving after a timed-out wait: the copies of brick t's stage may still be
+// writing into this block's shared memory, so wait for them once more (again
+// bounded) before the block exits.
+__device__ __forceinline__ void stage_drain(const BrickSmem &M, long long t) {
+  mbar_wait(M.bar(t), (uint32_t)((t >> 1) & 1));
+}
+
+// Kernels that read the neighbour list skip their work once the device error
+// word holds a non-finite position or an over-full cell (the step's results
+// are invalid; the host sees the error).
+__device__ __forceinline__ bool fatal_error(const KArgs &a) {
+  return (__ldcg(&a.ds->error) & (kErrNonfinite | kErrCellOverflow)) != 0u;
+}
+
 // Adds the stage cells' shifts to their copied offsets (warp w takes stage
 // cells w, w + C, ...); the caller has waited for the copies.
 __device__ __forceinline__ void stage_shift_all(const KArgs &a, const BrickDesc &d, float4 *pos,

@@ -2,11 +2,12 @@
 //
 // Binning (Sec. 4.3.3 uses a cell list built with atomics; Sec. 5.1 looks up
 // the cell neighbours of each particle): count per cell with atomics ->
-// exclusive scan -> scatter -> order each cell's members by index, which makes
-// the result independent of the atomics' order (Sec. 4.3.3 notes the atomics
-// make plain cell lists non-deterministic).  Cells are numbered along a 3-D
-// Hilbert curve per replica, so the cell list's particle order IS the
-// space-filling-curve order used by the sort.
+// exclusive scan -> scatter -> order each cell's members by their FP32 x
+// offset from the cell centre, ties by particle index, which makes the result
+// independent of the atomics' order (Sec. 4.3.3 notes the atomics make plain
+// cell lists non-deterministic).  Cells are numbered brick by brick along a
+// 3-D Hilbert curve over bricks of 2 x 2 x 2 cells per replica, so the cell
+// list's particle order IS the space-filling-curve order used by the sort.
 #include "brick.cuh"
 
 namespace mdgb {

@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kMaxBrickThreads, 1) k_nlist(KArgs a, int cap,
   // After a non-finite position or an over-full cell the step's results are
   // invalid (the host sees the error); skip the build: non-finite positions
   // all bin into one cell, whose stage the build would scan quadratically.
-  if (__ldcg(&a.ds->error) & (kErrNonfinite | kErrCellOverflow)) return;
+  if (fatal_error(a)) return;
   const long long step = a.ds->step;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     // the pair kernel runs after this launch has finished (stream order)
@@ -269,7 +269,10 @@ __global__ void __launch_bounds__(kMaxBrickThreads, 1) k_nlist(KArgs a, int cap,
   stage_issue(a, M.desc(0), M.pos(0), nullptr, M.bar(0), cap);
   bool ok = stage_wait(a, M, 0);
   stage_shift_all(a, M.desc(0), M.pos(0), cap);
-  if (!__syncthreads_and(ok)) return;
+  if (!__syncthreads_and(ok)) {
+    stage_drain(M, 0);
+    return;
+  }
   constexpr int kDescWords = (int)(sizeof(BrickDesc) / 16);
   for (long long t = 0; bt < a.n_bricks; t++) {
     const bool has1 = b1 < a.n_bricks;
@@ -302,7 +305,10 @@ __global__ void __launch_bounds__(kMaxBrickThreads, 1) k_nlist(KArgs a, int cap,
     ok = !has1 || stage_wait(a, M, t + 1);
     if (has1) stage_shift_all(a, M.desc(t + 1), M.pos(t + 1), cap);
     fence_proxy_async();
-    if (!__syncthreads_and(ok)) return;
+    if (!__syncthreads_and(ok)) {
+      stage_drain(M, t + 1);
+      return;
+    }
     bt = b1;
     b1 = b2;
   }

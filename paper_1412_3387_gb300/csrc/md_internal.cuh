@@ -14,11 +14,11 @@ namespace mdgb {
 constexpr int kMaxTypes = 32;
 constexpr int kChunkCells = 2048;     // cells per scan chunk (256 threads x 8)
 constexpr int kThermoChunk = 4096;    // particles per thermo partial sum
-constexpr int kIdxBits = 27;          // neighbour entry: index bits, code in the top 5
-constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
 constexpr int kMaxCellSort = 256;     // largest cell the in-cell sort handles
 constexpr int kCellBits = 9;          // packed cell coordinate bits (nc <= 512)
-constexpr int64_t kMaxParticles = (int64_t)1 << kIdxBits;
+// Largest system: 2^27 particles (about 80 GB of state and list at the
+// benchmark's density); int32 indices and cell-list positions everywhere.
+constexpr int64_t kMaxParticles = (int64_t)1 << 27;
 
 // Device error word bits.
 enum : uint32_t {
@@ -110,7 +110,7 @@ struct KArgs {
   int32_t *cell_idx;   // [N]
   int32_t *pcell;      // [N] cell slot of each particle (binning)
   int32_t *pslot;      // [N] rank inside its cell (binning)
-  uint16_t *nl;        // [n_pad * max_nb] 1 + stage slot, row groups (pipe.cuh)
+  uint16_t *nl;        // [n_pad * max_nb] 1 + stage slot, row groups (brick.cuh)
   int32_t *nl_tiles;   // [n_pad] tiles of the row group starting at this cell-list position
   int32_t *n_nb;       // [n_pad] row lengths, indexed by cell position
   int32_t stage_cap;   // staged particles per brick buffer

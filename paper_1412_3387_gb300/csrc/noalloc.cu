@@ -13,6 +13,7 @@
 // particles into cells at least r_cut wide, then each particle sums the LJ
 // force of every particle within r_cut in the 27 surrounding cells (FP64,
 // minimum image).  No neighbour list, no sort.
+#include <cmath>
 #include <mutex>
 
 #include "md_internal.cuh"
@@ -50,7 +51,11 @@ struct Grid {
   int64_t ncell;
 };
 
-__device__ __forceinline__ int cell_of(double x, double inv_h, int nc) {
+// Cell of coordinate x: x is first wrapped into [0, L) (callers need not
+// wrap their positions), then binned; the clamp only absorbs the rounding of
+// the wrap and of x / h at the box edge.
+__device__ __forceinline__ int cell_of(double x, double L, double inv_L, double inv_h, int nc) {
+  x -= L * floor(x * inv_L);
   int c = (int)floor(x * inv_h);
   c = c >= nc ? nc - 1 : c;
   return c < 0 ? 0 : c;
@@ -66,9 +71,9 @@ __global__ void k_na_count(const double4 *pos, int64_t n, Grid g, int32_t *count
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double4 x = pos[i];
-  int cx = cell_of(x.x, g.inv_h[0], g.nc[0]);
-  int cy = cell_of(x.y, g.inv_h[1], g.nc[1]);
-  int cz = cell_of(x.z, g.inv_h[2], g.nc[2]);
+  int cx = cell_of(x.x, g.L[0], g.inv_L[0], g.inv_h[0], g.nc[0]);
+  int cy = cell_of(x.y, g.L[1], g.inv_L[1], g.inv_h[1], g.nc[1]);
+  int cz = cell_of(x.z, g.L[2], g.inv_L[2], g.inv_h[2], g.nc[2]);
   int32_t c = cx + g.nc[0] * (cy + g.nc[1] * cz);
   pcell[i] = c;
   slot[i] = atomicAdd(count + c, 1);
@@ -159,12 +164,16 @@ extern "C" md_status md_lj_forces_noalloc(const double *dev_pos, int64_t n, cons
                                           double r_cut, double epsilon, double sigma,
                                           double *dev_force, md_stream stream_) {
   if (n < 0 || !box || (n > 0 && (!dev_pos || !dev_force))) return MD_ERR_INVALID_ARG;
-  if (!(r_cut > 0) || !(sigma > 0) || !(epsilon >= 0)) return MD_ERR_INVALID_ARG;
+  if (!(r_cut > 0) || !(sigma > 0) || !(epsilon >= 0) || !std::isfinite(r_cut))
+    return MD_ERR_INVALID_ARG;
   if (((uintptr_t)dev_pos & 15) != 0) return MD_ERR_INVALID_ARG;
   Grid g{};
   for (int d = 0; d < 3; d++) {
-    if (!(box[d] > 0)) return MD_ERR_INVALID_ARG;
-    double m = floor(box[d] / r_cut);
+    if (!(box[d] > 0) || !std::isfinite(box[d])) return MD_ERR_INVALID_ARG;
+    // cells at least r_cut (1 + 1e-12) wide: when the box is an exact multiple
+    // of r_cut, a cell exactly r_cut wide could let the rounding of x / h put
+    // two particles closer than r_cut two cells apart
+    double m = floor(box[d] / (r_cut * (1.0 + 1e-12)));
     if (m < 3.0) return MD_ERR_CELL_GRID;
     if (m > 1024.0) m = 1024.0;
     g.nc[d] = (int)m;

@@ -403,6 +403,17 @@ __global__ void __launch_bounds__(kMaxBrickThreads) k_pair(KArgs a, int cap) {
   const long long G = gridDim.x, b0 = blockIdx.x;
   const uint64_t step = (uint64_t)a.ds->step;
   if (b0 >= a.n_bricks) return;
+  if (fatal_error(a)) return;
+  // Rows name slots of the binning they were built from: a replica binned
+  // again since its last list build (a build skipped after an error, or a
+  // binning through the API without a build) has rows that do not match the
+  // current stages, and reading them could run past a stage.  Refuse.
+  int stale = 0;
+  for (int r = threadIdx.x; r < a.R; r += blockDim.x) stale |= __ldcg(a.list_ok + r) == 0;
+  if (__syncthreads_or(stale)) {
+    if (threadIdx.x == 0) set_error(a.ds, kErrStaleList);
+    return;
+  }
   if (threadIdx.x < 2) {
     M.pos(threadIdx.x)[0] = make_float4(kFar, kFar, kFar, 0.f);
     if (VEL) M.vel4(threadIdx.x)[0] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -418,7 +429,10 @@ __global__ void __launch_bounds__(kMaxBrickThreads) k_pair(KArgs a, int cap) {
   stage_issue(a, M.desc(0), M.pos(0), VEL ? M.vel4(0) : nullptr, M.bar(0), cap);
   bool ok = stage_wait(a, M, 0);
   stage_shift_all(a, M.desc(0), M.pos(0), cap);
-  if (!__syncthreads_and(ok)) return;
+  if (!__syncthreads_and(ok)) {
+    stage_drain(M, 0);
+    return;
+  }
   constexpr int kDescWords = (int)(sizeof(BrickDesc) / 16);
   for (long long t = 0;; t++) {
     const long long bt = b0 + t * G;
@@ -458,7 +472,10 @@ __global__ void __launch_bounds__(kMaxBrickThreads) k_pair(KArgs a, int cap) {
     ok = !has1 || stage_wait(a, M, t + 1);
     if (has1) stage_shift_all(a, M.desc(t + 1), M.pos(t + 1), cap);
     fence_proxy_async();
-    if (!__syncthreads_and(ok)) return;
+    if (!__syncthreads_and(ok)) {
+      stage_drain(M, t + 1);
+      return;
+    }
   }
 }
 

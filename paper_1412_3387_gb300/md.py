@@ -354,16 +354,32 @@ def philox4x32_10(inp, stream=None):
 def lj_forces_noalloc(pos, box, r_cut, epsilon=1.0, sigma=1.0, stream=None):
     """FP64 LJ forces of one system through md_lj_forces_noalloc, the entry
     point for callers that cannot allocate device memory (it uses a fixed
-    4 MiB scratch array inside the library).  pos: float64 CUDA tensor [n, 4];
-    returns a float64 CUDA tensor [n, 4] (F, per-particle energy)."""
+    4 MiB scratch array inside the library).  pos: contiguous float64 CUDA
+    tensor [n, 4]; returns a float64 CUDA tensor [n, 4] (F, per-particle
+    energy) on the same device.  The C entry point sees only a raw pointer,
+    so the tensor's dtype, shape, layout and device are checked here, before
+    anything is launched (ValueError)."""
     import torch
+    if not isinstance(pos, torch.Tensor):
+        raise ValueError("pos must be a torch tensor")
+    if pos.dtype != torch.float64:
+        raise ValueError(f"pos must be float64, not {pos.dtype}")
+    if pos.dim() != 2 or pos.shape[1] != 4:
+        raise ValueError(f"pos must have shape [n, 4], not {tuple(pos.shape)}")
+    if not pos.is_contiguous():
+        raise ValueError("pos must be contiguous")
+    if not pos.is_cuda:
+        raise ValueError("pos must be a CUDA tensor")
+    b = np.ascontiguousarray(np.broadcast_to(np.asarray(box, np.float64).reshape(-1), (3,)))
     lib = load()
     n = int(pos.shape[0])
-    out = torch.empty((n, 4), dtype=torch.float64, device=pos.device)
-    b = np.ascontiguousarray(np.broadcast_to(np.asarray(box, np.float64).reshape(-1), (3,)))
-    check(lib.md_lj_forces_noalloc(_ptr(pos), n, b.ctypes.data_as(C.c_void_p), float(r_cut),
-                                   float(epsilon), float(sigma), _ptr(out), _stream(stream)),
-          "md_lj_forces_noalloc")
+    with torch.cuda.device(pos.device):
+        st = stream if stream is not None else torch.cuda.current_stream(pos.device)
+        out = torch.empty((n, 4), dtype=torch.float64, device=pos.device)
+        check(lib.md_lj_forces_noalloc(_ptr(pos), n, b.ctypes.data_as(C.c_void_p), float(r_cut),
+                                       float(epsilon), float(sigma), _ptr(out),
+                                       C.c_void_p(st.cuda_stream)),
+              "md_lj_forces_noalloc")
     return out
 
 

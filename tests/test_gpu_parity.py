@@ -341,21 +341,44 @@ def test_thermo_matches_oracle_and_is_reproducible():
         assert a[k] == pytest.approx(th_ref[name], rel=1e-11, abs=1e-9), name
 
 
-def test_sort_matches_oracle_order_and_keeps_forces():
+def brick_keys(pos, L, r_list):
+    """Hilbert index of each particle's brick of 2 x 2 x 2 cells (oracle)."""
+    nc = oracle.cells_per_dim(L[0], r_list)
+    cc = oracle.cell_coords(pos, L, [nc] * 3)
+    bits = 1
+    while (1 << bits) < (nc + 1) // 2:
+        bits += 1
+    keys = np.array([oracle.hilbert3(x >> 1, y >> 1, z >> 1, bits) for x, y, z in cc])
+    return keys, cc
+
+
+def test_sort_follows_the_curve_and_keeps_forces():
+    """The sort's order is a permutation along which the particles' brick keys
+    (the oracle's Hilbert index) never decrease and each cell's members are
+    contiguous; the oracle order has the same key sequence.  The order inside
+    a brick is the library's own (not fixed by the method), so it is checked
+    only through these properties and through the forces, which must not
+    depend on it."""
     st = lj_state(n=4000, jitter=0.3)
     rng = np.random.default_rng(1)
     perm = rng.permutation(st.n)  # scramble the input order
     for k in ("pos", "vel", "image"):
         setattr(st, k, getattr(st, k)[perm])
     L = st.box[0]
-    order = oracle.sfc_order(st.pos, L, 2.8)
     s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005)
     s.build_cells()
     s.sort()
     s.prepare()
     g = s.state_numpy()
-    assert np.array_equal(g["tag"], order)  # tags were 0..N-1 in input order
+    order = g["tag"]  # tags were 0..N-1 in input order
+    assert sorted(order.tolist()) == list(range(st.n))
     assert np.array_equal(g["pos"], st.pos[order])
+    keys, cc = brick_keys(st.pos, L, 2.8)
+    assert np.all(np.diff(keys[order]) >= 0)
+    assert np.array_equal(keys[order], keys[oracle.sfc_order(st.pos, L, 2.8)])
+    cid = [tuple(c) for c in cc[order]]
+    runs = [cid[0]] + [cid[k] for k in range(1, len(cid)) if cid[k] != cid[k - 1]]
+    assert len(runs) == len(set(runs))  # every cell one contiguous run
     f = s.forces().cpu().numpy()
     ref, _, absf = oracle.lj_forces(st.pos, L, 2.5)
     fp64_force_check(f, ref[order], absf[order])
@@ -411,6 +434,25 @@ def test_rebuild_flag_follows_half_skin_rule():
     assert step_and_check_rebuild() == 1
 
 
+def test_pair_refuses_a_list_of_an_older_binning():
+    """Host-made failure: a replica binned again (its rebuild flag raised by a
+    particle that moved more than half the skin) but not listed again.  The
+    pair kernel must refuse the stale rows (MD_ERR_STATE in the error word)
+    instead of reading slots of the old stages; forces are left as they were."""
+    st = lj_state(n=2048, jitter=0.05)
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.4, dt=0.005)
+    s.prepare()
+    f0 = s.forces().cpu().numpy()
+    s.vel.zero_()
+    s.vel[5, 1] = 0.3 / 0.005
+    s.integrate(1)
+    s.build_cells(force=False)  # bins the flagged replica; no list build
+    s.compute_pair()
+    code, _ = s.poll_error()
+    assert code == 8, code  # MD_ERR_STATE
+    assert np.array_equal(s.forces().cpu().numpy(), f0)
+
+
 def test_nlist_overflow_is_reported():
     st = lj_state(n=2048)
     s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, max_nb=32)
@@ -439,18 +481,36 @@ def test_nonfinite_position_is_reported_and_stops_list_builds():
     assert not np.isfinite(pos[123, :3]).all()
 
 
+def oracle_drifts():
+    """The CPU oracle's own drift on the same eight seeded trajectories
+    (tests/golden/nve_drift_oracle.txt, written by make_nve_drift_oracle.py)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "nve_drift_oracle.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    return {int(r[0]): float(r[1]) for r in rows}
+
+
 @pytest.mark.parametrize("prec", ("fp64", "mixed"))
 def test_nve_energy_drift(prec):
     """Shifted-energy drift over 1e4 steps at dt = 0.005 after 1000
-    equilibration steps (N = 4000 fcc start, T = 1.44).  A single trajectory's
-    least-squares slope is dominated by slow energy fluctuations (the oracle's
-    own runs give 2.5e-5 .. 8.6e-5 for seeds 14..17; the FP64 path 6e-6 ..
-    7e-5 for seeds 14..21), so the bound applies to the mean over eight seeded
-    realizations; each one stays below 3e-4.  The mixed path's FP32
-    separations (positions relative to a brick centre, up to two cells away)
-    about double the mean (8.8e-5 for seeds 14..21)."""
+    equilibration steps (N = 4000 fcc start, T = 1.44), seeds 14..21.
+
+    Reading of the bound "drift < 1e-4 per particle over 1e4 steps": a single
+    trajectory's least-squares slope is dominated by slow energy fluctuations,
+    and the exact FP64 method itself (the oracle, same seeds) exceeds 1e-4 on
+    one of the eight (seed 21: 1.13e-4; mean 5.5e-5).  So the bound applies
+    to the mean over the eight seeded realizations, and each trajectory stays
+    below twice the oracle's largest single-trajectory drift.  Momentum: the
+    FP64 path conserves it to 1e-8; the mixed path's pair forces f_ij and
+    f_ji are rounded separately in FP32, a random walk bounded by
+    20 x dt sqrt(steps) 2^-24 sqrt(n_pairs) f_rms."""
+    ref = oracle_drifts()
+    seeds = sorted(ref)
+    assert seeds == list(range(14, 22))
+    assert np.mean(list(ref.values())) < 1e-4  # the reading holds for the method itself
+    ceiling = 2.0 * max(ref.values())
     drifts = []
-    for seed in range(14, 22):
+    for seed in seeds:
         st = inputs.lj_fluid(4000, 0.8442, 1.44, seed=seed)
         s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, precision=prec,
                         shift_energy=True, thermo_period=10, graph_steps=100, sort_period=200)
@@ -462,10 +522,18 @@ def test_nve_energy_drift(prec):
         drifts.append(abs(np.polyfit(t, e, 1)[0]) * 1e4 * 0.005)
         assert np.max(np.abs(e - e[0])) < 1e-3
         p_tot = np.abs(th[:, 5:8]).max()
-        assert p_tot < (1e-8 if prec == "fp64" else 1.0), p_tot
+        if prec == "fp64":
+            assert p_tot < 1e-8, p_tot
+        else:
+            f = s.forces().cpu().numpy()[:, :3]
+            counts, _ = s.nlist()
+            n_pairs = float(counts.sum().item()) / 2
+            f_rms = math.sqrt(float(np.mean(np.sum(f * f, axis=1))))
+            bound = 20 * 0.005 * math.sqrt(11000) * 2.0 ** -24 * math.sqrt(n_pairs) * f_rms
+            assert p_tot < bound, (p_tot, bound)
         s.close()
     assert np.mean(drifts) < 1e-4, drifts
-    assert max(drifts) < 3e-4, drifts
+    assert max(drifts) < ceiling, (drifts, ceiling)
 
 
 def test_batched_replicas_equal_standalone_runs():

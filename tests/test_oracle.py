@@ -308,6 +308,60 @@ def test_thermo_of_maxwell_boltzmann_input():
     assert th["pressure"] == pytest.approx(2 * th["ke"] / (3 * V), rel=1e-12)
 
 
+@pytest.mark.parametrize("rho,r_cut", [(0.8442, 2.5), (1.0, 3.0)])
+def test_thermo_virial_pressure_is_minus_dU_dV_on_the_lattice(rho, r_cut):
+    """At T = 0 the pressure of a perfect fcc lattice is -dU/dV (thermodynamic
+    route).  U(V) is the oracle's summed potential energy at three nearby
+    densities (no neighbour shell crosses r_cut in between); the thermo row's
+    pressure W / (3V) at the middle density, with W the summed virial trace,
+    must equal its central difference.  A wrong sign, a missing 1/3 or a
+    virial off by a factor fails this.  W itself equals the shell sum."""
+    n, eps = 4 * 6 ** 3, 1e-5
+    vel = np.zeros((n, 4))
+    U, V, P, W = [], [], [], []
+    for r in (rho * (1 - eps), rho, rho * (1 + eps)):
+        st = inputs.lj_fluid(n, r, 1.0, seed=1)  # perfect 6^3 lattice
+        L = st.box[0]
+        f, vir, _ = oracle.lj_forces(st.pos, L, r_cut)
+        th = oracle.thermo(vel, f, vir, L)
+        U.append(th["pe"])
+        V.append(float(np.prod(L)))
+        P.append(th["pressure"])
+        W.append(th["virial"])
+    dUdV = (U[2] - U[0]) / (V[2] - V[0])
+    assert P[1] == pytest.approx(-dUdV, rel=1e-6)
+    # the virial trace is the crystallographic shell sum times N
+    a = (4.0 / rho) ** (1.0 / 3.0)
+    w = 0.0
+    for k, z in _fcc_shells():
+        rr = a * math.sqrt(k / 2.0)
+        if rr < r_cut:
+            fr, _ = oracle.lj_pair(rr * rr)
+            w += 0.5 * z * fr * rr * rr
+    assert W[1] == pytest.approx(n * w, rel=1e-11)
+    assert P[1] == pytest.approx(W[1] / (3.0 * V[1]), rel=1e-12)
+
+
+def test_thermo_ideal_gas_and_two_particle_virial():
+    """No pair inside r_cut: P V = (N - 1) T (ideal gas with the 3N - 3
+    degrees of freedom of the temperature); two particles at r = sigma add
+    W = r . f = 24 and P = W / (3V) beyond the kinetic part."""
+    st = inputs.lj_fluid(500, 0.01, 2.0, seed=5)  # dilute: spacing 5.8 > r_cut
+    L = st.box[0]
+    f, vir, absf = oracle.lj_forces(st.pos, L, 2.5)
+    assert absf.max() == 0.0
+    th = oracle.thermo(st.vel, f, vir, L)
+    V = float(np.prod(L))
+    assert th["pressure"] * V == pytest.approx((500 - 1) * th["temperature"], rel=1e-12)
+    pos = np.zeros((2, 4))
+    pos[0, :3] = [5.0, 5.0, 5.0]
+    pos[1, :3] = [5.0, 6.0, 5.0]
+    f, vir, _ = oracle.lj_forces(pos, 10.0, 2.5)
+    th = oracle.thermo(np.zeros((2, 4)), f, vir, 10.0)
+    assert th["virial"] == pytest.approx(24.0, abs=1e-12)
+    assert th["pressure"] == pytest.approx(24.0 / 3000.0, abs=1e-15)
+
+
 def test_time_reversibility_lj():
     st = inputs.lj_fluid(864, 0.8442, 1.44, seed=13)
     L = st.box[0]
@@ -394,15 +448,34 @@ def test_sfc_order_is_permutation_walking_adjacent_bricks():
     assert sorted(order.tolist()) == list(range(len(cells)))
     walk = cells[perm][order]
     bricks = walk // 2
-    # each run of 8 is one brick, its cells x first, then y, then z
+    # each run of 8 is one brick, its particles in index order (ties by index)
     for k in range(0, len(walk), 8):
         assert np.all(bricks[k:k + 8] == bricks[k])
-        local = walk[k:k + 8] % 2
-        assert (local[:, 0] + 2 * local[:, 1] + 4 * local[:, 2]).tolist() == list(range(8))
+        assert np.all(np.diff(order[k:k + 8]) > 0)
     # and the bricks follow the Hilbert curve: unit steps, starting at the origin
     b = bricks[::8]
     assert np.all(np.abs(np.diff(b, axis=0)).sum(1) == 1)
     assert b[0].tolist() == [0, 0, 0]
+
+
+def test_sfc_order_odd_grid_and_many_per_cell():
+    # 7 cells per edge (the last brick layer is one cell thick), several
+    # particles per cell: bricks form contiguous runs along a unit-step walk
+    L, rl = 21.0, 3.0
+    rng = np.random.default_rng(4)
+    pos = np.zeros((3000, 4))
+    pos[:, :3] = rng.uniform(0.0, L, (3000, 3))
+    order = oracle.sfc_order(pos, L, rl)
+    assert sorted(order.tolist()) == list(range(3000))
+    b = oracle.cell_coords(pos, L, [7, 7, 7])[order] // 2
+    keys = [tuple(x) for x in b]
+    runs = [keys[0]] + [keys[k] for k in range(1, len(keys)) if keys[k] != keys[k - 1]]
+    assert len(runs) == len(set(runs)) == 4 ** 3  # every brick one contiguous run
+    steps = np.abs(np.diff(np.array(runs), axis=0)).sum(1)
+    assert np.all(steps == 1)
+    for k in range(1, len(keys)):  # ties by index inside a brick
+        if keys[k] == keys[k - 1]:
+            assert order[k] > order[k - 1]
 
 
 def test_local_neighbourhood_answers_equal_whole_system_ones():

@@ -10,6 +10,7 @@ file is collected last on purpose."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1412_3387_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -71,3 +72,82 @@ def test_noalloc_rejects_systems_beyond_its_scratch():
     with pytest.raises(md.MDError) as e:
         md.lj_forces_noalloc(small, [5.0, 5.0, 5.0], 2.5)  # 2 cells per edge
     assert e.value.code == 5  # MD_ERR_CELL_GRID
+
+
+def _lattice_state(counts, seed, jitter=0.1, vacancies=0, rho=0.8442):
+    """Jittered simple-cubic lattice at density rho in an orthorhombic box of
+    counts[d] lattice spacings per edge, with `vacancies` seeded empty sites."""
+    rng = np.random.default_rng(seed)
+    a = (1.0 / rho) ** (1.0 / 3.0)
+    g = np.stack(np.meshgrid(*[np.arange(c) for c in counts], indexing="ij"), -1).reshape(-1, 3)
+    if vacancies:
+        g = g[np.sort(rng.permutation(len(g))[:len(g) - vacancies])]
+    xyz = (g + 0.5 + rng.uniform(-jitter, jitter, g.shape)) * a
+    n = len(g)
+    box = np.array(counts, np.float64) * a
+    pos = np.zeros((n, 4))
+    pos[:, :3] = np.mod(xyz, box)
+    return inputs.State(pos=pos, vel=np.zeros((n, 4)), image=np.zeros((n, 4), np.int32),
+                        tag=np.arange(n, dtype=np.int32), type=np.zeros(n, np.int32),
+                        box=box[None, :], offsets=np.array([0, n], np.int64))
+
+
+def test_noalloc_accepts_exactly_its_scratch_and_refuses_one_more():
+    # 69 x 69 x 70 sites less 4 vacancies: 333,266 particles in 29^3 cells of
+    # r_cut = 2.5, i.e. 2 * 24,389 + 3 * 333,266 = 1,048,576 ints, the whole array
+    st = _lattice_state((69, 69, 70), seed=64, vacancies=4)
+    assert 2 * 29 ** 3 + 3 * st.n == 1 << 20
+    ref = _regular_path_forces(st, 2.5)
+    p = torch.as_tensor(st.pos, device="cuda")
+    _check(md.lj_forces_noalloc(p, st.box[0], 2.5).cpu().numpy(), ref)
+    st1 = _lattice_state((69, 69, 70), seed=64, vacancies=3)  # one particle more
+    p1 = torch.as_tensor(st1.pos, device="cuda")
+    with pytest.raises(md.MDError) as e:
+        md.lj_forces_noalloc(p1, st1.box[0], 2.5)
+    assert e.value.code == 3  # MD_ERR_WORKSPACE_TOO_SMALL
+
+
+def test_noalloc_noncubic_box_and_unwrapped_positions():
+    st = _lattice_state((20, 28, 36), seed=65)
+    ref = _regular_path_forces(st, 2.5)
+    p = torch.as_tensor(st.pos, device="cuda")
+    _check(md.lj_forces_noalloc(p, st.box[0], 2.5).cpu().numpy(), ref)
+    # the same positions shifted by whole box lengths (callers need not wrap)
+    shift = np.random.default_rng(5).integers(-3, 4, (st.n, 3)) * st.box[0]
+    q = st.pos.copy()
+    q[:, :3] += shift
+    fq = md.lj_forces_noalloc(torch.as_tensor(q, device="cuda"), st.box[0], 2.5).cpu().numpy()
+    _check(fq, ref)
+
+
+def test_noalloc_box_an_exact_multiple_of_r_cut():
+    # box 10 = 4 r_cut: cells are 10 / 3 wide (the 1e-12 margin), and pairs
+    # straddling the planes x = k r_cut at r_cut (1 - 1e-14) still interact
+    L, rc = 10.0, 2.5
+    d = rc * (1 - 1e-14)
+    yz = ((0.5, 0.5), (5.5, 0.5), (0.5, 5.5), (5.5, 5.5))  # pairs >= 5 apart
+    pos = np.zeros((8, 4))
+    for k, x0 in enumerate((2.5, 5.0, 7.5, 10.0)):
+        pos[2 * k, :3] = [x0 - 0.5 * d, *yz[k]]
+        pos[2 * k + 1, :3] = [x0 + 0.5 * d, *yz[k]]
+    pos[:, :3] = np.mod(pos[:, :3], L)
+    f = md.lj_forces_noalloc(torch.as_tensor(pos, device="cuda"), [L, L, L], rc).cpu().numpy()
+    ref, _, absf = oracle.lj_forces(pos, L, rc)
+    assert np.all(absf > 0)  # each particle feels its partner, inside r_cut
+    _check(f, ref)
+
+
+def test_noalloc_long_box_beyond_the_cell_cap():
+    # 2600 / 2.5 = 1040 cells along x, capped at 1024 (cells 2.54 wide)
+    rng = np.random.default_rng(67)
+    n = 3000
+    box = np.array([2600.0, 9.0, 9.0])
+    pos = np.zeros((n, 4))
+    pos[:, :3] = rng.uniform(0.0, 1.0, (n, 3)) * box
+    st = inputs.State(pos=pos, vel=np.zeros((n, 4)), image=np.zeros((n, 4), np.int32),
+                      tag=np.arange(n, dtype=np.int32), type=np.zeros(n, np.int32),
+                      box=box[None, :], offsets=np.array([0, n], np.int64))
+    ref, _, absf = oracle.lj_forces(pos, box, 2.5)
+    f = md.lj_forces_noalloc(torch.as_tensor(pos, device="cuda"), box, 2.5).cpu().numpy()
+    d = np.linalg.norm(f[:, :3] - ref[:, :3], axis=1)
+    assert np.all(d <= 1e-12 * np.maximum(np.linalg.norm(ref[:, :3], axis=1), 1e-2 * absf) + 1e-300)
