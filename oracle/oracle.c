@@ -47,7 +47,10 @@ static double acc_get(const acc_t *a) { return a->s + a->c; }
  * neighbours of particle i).                                                */
 
 int32_t orc_cells_per_dim(double L, double r_list) {
-    double m = floor(L / r_list);
+    /* cells at least r_list (1 + 1e-12) wide, so that rounding in x / h
+     * cannot put two particles closer than r_list two cells apart even when
+     * L is an exact multiple of r_list */
+    double m = floor(L / (r_list * (1.0 + 1e-12)));
     if (m > 512.0) m = 512.0;
     if (m < 3.0) return 0;
     return (int32_t)m;

@@ -38,7 +38,9 @@ extern "C" {
 #endif
 
 /* Number of cells per box edge for a cell list of minimum width r_list:
- * floor(L / r_list), capped at 512.  Returns 0 when fewer than 3 fit. */
+ * floor(L / (r_list (1 + 1e-12))), capped at 512 (the margin keeps cells
+ * strictly wider than r_list when L is an exact multiple of it).  Returns 0
+ * when fewer than 3 fit. */
 int32_t orc_cells_per_dim(double L, double r_list);
 
 /* Integer cell coordinates of every particle, cell[i][d] in [0, nc[d]). */

@@ -141,7 +141,10 @@ md_status make_plan(const md_params *p, Plan &pl) {
     double hmax = 0;
     for (int d = 0; d < 3; d++) {
       const double L = p->box[3 * r + d];
-      double m = std::floor(L / rl);
+      // cells at least r_list (1 + 1e-12) wide: with cells exactly r_list wide
+      // (a box an exact multiple of r_list), the rounding of x / h could put
+      // two particles closer than r_list two cells apart
+      double m = std::floor(L / (rl * (1.0 + 1e-12)));
       if (m > 512.0) m = 512.0;
       if (m < 3.0) return MD_ERR_CELL_GRID;
       rp.nc[d] = (int32_t)m;
@@ -150,14 +153,47 @@ md_status make_plan(const md_params *p, Plan &pl) {
       rp.h[d] = L / (double)rp.nc[d];
       rp.half_h[d] = 0.5 * rp.h[d];
       rp.inv_h[d] = (double)rp.nc[d] / L;
-      rp.hf[d] = (float)rp.h[d];
       rp.Lf[d] = (float)L;
       hmax = std::max(hmax, rp.h[d]);
     }
-    // FP32 r^2 error bound: |o| <= (h + skin) / 2 per coordinate; each
-    // separation component carries at most ~7 roundings of 2^-24 (h + skin),
-    // so |dr^2| < 28 * 2^-24 (h + skin)^2; the band doubles that.
-    rp.band = (float)(64.0 * std::ldexp(1.0, -24) * (hmax + p->r_skin) * (hmax + p->r_skin));
+    // Stage frame (brick.cuh), per axis: the smallest power-of-two grid gq for
+    // which every frame offset, |o| <= h/2 + skin/2 + drift, stays below
+    // 2^22 gq (frame_offset's rounding trick) and every stage coordinate,
+    // |o| + 1.5 hq + |wq|, below 2^24 gq (exact FP32 sums and differences).
+    // hq = h rounded to a multiple of 2 gq; the frame centres (c + 1/2) hq
+    // drift from the cell centres by at most nc |hq - h|.
+    double gmax = 0.0, drift_max = 0.0;
+    for (int d = 0; d < 3; d++) {
+      const double h = rp.h[d], L = rp.L[d];
+      const int nc = rp.nc[d];
+      double g = std::ldexp(1.0, -40), hq = h, wq = 0.0, drift = 0.0;
+      for (;;) {
+        hq = 2.0 * g * std::nearbyint(h / (2.0 * g));
+        wq = g * std::nearbyint((L - nc * hq) / g);
+        drift = nc * std::fabs(hq - h) + g;
+        const double omax = 0.5 * h + 0.5 * p->r_skin + drift;
+        if (omax < std::ldexp(g, 22) && omax + 1.5 * hq + std::fabs(wq) < std::ldexp(g, 24)) break;
+        g *= 2.0;
+      }
+      rp.gq[d] = (float)g;
+      rp.hq[d] = (float)hq;
+      rp.wq[d] = (float)wq;
+      rp.cq[d] = (float)(1.5 * std::ldexp(g, 23));
+      gmax = std::max(gmax, g);
+      drift_max = std::max(drift_max, drift);
+    }
+    rp.weps = (float)(1e-4 * hmax + 2.0 * drift_max + 4.0 * gmax);
+    // FP32 r^2 uncertainty: each separation component is exact up to the grid
+    // rounding of two offsets and of wq (<= 1.5 gq), and r^2 = dx^2 + dy^2 +
+    // dz^2 is rounded three times, so near r_list
+    //   |dr^2| <= 2 r_list sqrt(3) 1.5 gq + 3 2^-24 r_list^2.
+    // The band is the larger of 64 2^-24 (h + skin)^2 and four times that.
+    {
+      const double rl = p->r_cut + p->r_skin;
+      const double err = 2.0 * rl * std::sqrt(3.0) * 1.5 * gmax + 3.0 * std::ldexp(rl * rl, -24);
+      rp.band = (float)std::max(64.0 * std::ldexp(1.0, -24) * (hmax + p->r_skin) * (hmax + p->r_skin),
+                                4.0 * err);
+    }
     rp.volume = rp.L[0] * rp.L[1] * rp.L[2];
     rp.ncell = rp.nc[0] * rp.nc[1] * rp.nc[2];
     rp.nchunk = (rp.ncell + kChunkCells - 1) / kChunkCells;
@@ -462,7 +498,8 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
     for (int c = 0; c < rp.nchunk; c++) chunk_rep[rp.chunk0 + c] = r;
     for (int c = 0; c < rp.ntchunk; c++) tchunk_rep[rp.tchunk0 + c] = r;
     for (int d = 0, off = 0; d < 3; off += rp.nc[d], d++)
-      for (int c = 0; c < rp.nc[d]; c++) ctab[rp.ctab0 + off + c] = std::fma((double)c, rp.h[d], rp.half_h[d]);
+      for (int c = 0; c < rp.nc[d]; c++)  // exact: (c + 1/2) hq and cq are multiples of gq
+        ctab[rp.ctab0 + off + c] = ((double)c + 0.5) * (double)rp.hq[d] - (double)rp.cq[d];
     const int nb[3] = {(rp.nc[0] + 1) / 2, (rp.nc[1] + 1) / 2, (rp.nc[2] + 1) / 2};
     const int nmax = std::max(nb[0], std::max(nb[1], nb[2]));
     int bits = 1;
@@ -494,7 +531,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
         rank[rp.cell0 + cell_lin(x, y, z)] = k++;
         mask |= 1 << q;
       }
-      binfo[B] = make_int4((int)(rp.cell0 + first), mask, r, 0);
+      binfo[B] = make_int4((int)(rp.cell0 + first), mask, r, bx | (by << 10) | (bz << 20));
       brep[B] = r;
     }
     for (int64_t bi = 0; bi < rp.nbrick; bi++) {

@@ -10,11 +10,22 @@
 // 2 b - 1 + s per axis, periodically wrapped; on very small grids a cell can
 // appear twice, at two periodic images).  Each home cell's 27 neighbour
 // cells form a 3 x 3 x 3 sub-block of the stage.  The stage holds the FP32
-// positions of all members of the 64 stage cells relative to the brick centre:
-// member offset from its own cell centre (pos4f, kept in cell-list order so
-// each cell is a contiguous range) plus (s - 1.5) h per axis.  Then
+// positions of all members of the 64 stage cells relative to the brick
+// origin: member offset o from its own frame centre (pos4f, kept in
+// cell-list order so each cell is a contiguous range) plus the stage cell's
+// shift (s - 1.5) hq, plus or minus wq for a cell seen across the periodic
+// boundary.  Then
 //   x_i - x_j = stage[slot of i] - stage[slot of j]
 // for any home particle i and stage particle j of its stencil.
+//
+// Exactness.  o, hq and wq are multiples of the replica's grid gq (a power of
+// two) and every stage coordinate and separation stays below 2^24 gq in
+// magnitude, so all of them are computed exactly in FP32: the only error is
+// the rounding of each offset to the grid (and of wq), at most 1.5 gq per
+// separation component.  A pair's separation seen from i's brick is then
+// exactly minus the one seen from j's, and the pair forces the two bricks
+// compute are exactly opposite (Newton's third law holds to the last bit,
+// so the FP32 forces conserve momentum up to the per-particle sums' rounding).
 //
 // A persistent block walks bricks b, b + G, b + 2G, ... with two stage
 // buffers: while its warps compute brick t, brick t + 1's stage is in flight
@@ -63,7 +74,8 @@ struct BrickDesc {
   int hoff[9];    // the brick's particle q lies in its i-th existing cell for hoff[i] <= q < hoff[i+1]
   int hcell[8];   // stage cell of the brick's i-th existing cell
   int hbase[8];   // staged slot of the particle at cell-list position p of that cell: p + hbase[i]
-  int pad[2];
+  int bc;         // brick coordinates bx | by << 10 | bz << 20 (periodic images of the stage)
+  int pad;
 };
 static_assert(sizeof(BrickDesc) == 640, "BrickDesc layout");
 
@@ -95,9 +107,20 @@ __device__ __forceinline__ int stage_cell_of(const BrickDesc &d, int s) {
   return k;
 }
 
-__device__ __forceinline__ float3 stage_shift(const Rep &rp, int s) {
-  return make_float3(((float)(s & 3) - 1.5f) * rp.hf[0], ((float)((s >> 2) & 3) - 1.5f) * rp.hf[1],
-                     ((float)(s >> 4) - 1.5f) * rp.hf[2]);
+// Shift of stage cell coordinate s (0..3) along axis ax for a brick at brick
+// coordinate b: (s - 1.5) hq, minus wq if the cell is the periodic image
+// below the box, plus wq above it.  Both terms are multiples of gq, so the
+// shift and its sum with an offset are exact.
+__device__ __forceinline__ float stage_shift1(const Rep &rp, int ax, int s, int b) {
+  const int c = 2 * b - 1 + s;
+  const float w = c < 0 ? -rp.wq[ax] : c >= rp.nc[ax] ? rp.wq[ax] : 0.f;
+  return ((float)s - 1.5f) * rp.hq[ax] + w;
+}
+
+__device__ __forceinline__ float3 stage_shift(const Rep &rp, int s, int bc) {
+  return make_float3(stage_shift1(rp, 0, s & 3, bc & 1023),
+                     stage_shift1(rp, 1, (s >> 2) & 3, (bc >> 10) & 1023),
+                     stage_shift1(rp, 2, s >> 4, bc >> 20));
 }
 
 // ---- asynchronous copies (PTX) ---------------------------------------------
@@ -297,11 +320,9 @@ __device__ __forceinline__ void stage_shift_all(const KArgs &a, const BrickDesc 
   if (d.off[64] > cap) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, C = blockDim.x >> 5;
   const Rep &rp = a.rep[d.r];
-  const float hx = rp.hf[0], hy = rp.hf[1], hz = rp.hf[2];  // loaded once, not per cell
   for (int s = warp; s < kStageCells; s += C) {
     const int o = d.off[s], n = d.off[s + 1] - o;
-    const float3 h = make_float3(((float)(s & 3) - 1.5f) * hx, ((float)((s >> 2) & 3) - 1.5f) * hy,
-                                 ((float)(s >> 4) - 1.5f) * hz);
+    const float3 h = stage_shift(rp, s, d.bc);
     for (int m = lane; m < n; m += 32) {
       const float4 v = pos[1 + o + m];
       pos[1 + o + m] = make_float4(v.x + h.x, v.y + h.y, v.z + h.z, v.w);
@@ -323,7 +344,7 @@ struct StageSrc {
     if (e == 0u) return make_float4(kFar, kFar, kFar, 0.f);
     const int s = (int)e - 1, k = stage_cell_of(d, s);
     float4 v = __ldg(a.pos4f + d.start[k] + (s - d.off[k]));
-    const float3 h = stage_shift(rp, k);
+    const float3 h = stage_shift(rp, k, d.bc);
     v.x += h.x;
     v.y += h.y;
     v.z += h.z;

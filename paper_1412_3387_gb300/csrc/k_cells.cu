@@ -159,9 +159,9 @@ __device__ __forceinline__ void k_bin_scatter_one(const KArgs &a, int64_t i, int
   int cy = cell_coord(x.y, rp.inv_h[1], rp.nc[1]);
   int cz = cell_coord(x.z, rp.inv_h[2], rp.nc[2]);
   float4 o;
-  o.x = frame_offset(x.x, cell_centre(a, rp, 0, cx), rp.Lf[0], rp.L[0]);
-  o.y = frame_offset(x.y, cell_centre(a, rp, 1, cy), rp.Lf[1], rp.L[1]);
-  o.z = frame_offset(x.z, cell_centre(a, rp, 2, cz), rp.Lf[2], rp.L[2]);
+  o.x = frame_offset(x.x, cell_centre(a, rp, 0, cx), rp.cq[0], rp.Lf[0], rp.L[0]);
+  o.y = frame_offset(x.y, cell_centre(a, rp, 1, cy), rp.cq[1], rp.Lf[1], rp.L[1]);
+  o.z = frame_offset(x.z, cell_centre(a, rp, 2, cz), rp.cq[2], rp.Lf[2], rp.L[2]);
   o.w = __uint_as_float(pack_cell(cx, cy, cz, a.type[i]));
   a.oref[i] = o;
 }
@@ -290,6 +290,7 @@ __global__ void k_brick_desc(KArgs a, int force) {
     d.r = info.z;
     d.hstart = a.cell_start[info.x];
     d.hmask = info.y;
+    d.bc = info.w;
   }
 }
 

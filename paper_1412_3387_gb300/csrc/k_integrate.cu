@@ -103,9 +103,9 @@ __global__ void k_integrate1(KArgs a, double hk) {
     const float4 ref = a.oref[i];
     float4 o = ref;
     const uint32_t w = __float_as_uint(ref.w);
-    o.x = frame_offset(x.x, cell_centre(a, rp, 0, cell_x(w)), rp.Lf[0], rp.L[0]);
-    o.y = frame_offset(x.y, cell_centre(a, rp, 1, cell_y(w)), rp.Lf[1], rp.L[1]);
-    o.z = frame_offset(x.z, cell_centre(a, rp, 2, cell_z(w)), rp.Lf[2], rp.L[2]);
+    o.x = frame_offset(x.x, cell_centre(a, rp, 0, cell_x(w)), rp.cq[0], rp.Lf[0], rp.L[0]);
+    o.y = frame_offset(x.y, cell_centre(a, rp, 1, cell_y(w)), rp.cq[1], rp.Lf[1], rp.L[1]);
+    o.z = frame_offset(x.z, cell_centre(a, rp, 2, cell_z(w)), rp.cq[2], rp.Lf[2], rp.L[2]);
     // the FP32 copies are kept in cell-list order
     const int64_t p = __ldg(a.ident + r) ? i : (int64_t)a.cellpos[i];
     a.pos4f[p] = o;
@@ -301,9 +301,9 @@ __global__ void k_init_frames(KArgs a) {
   const int cy = cell_coord(x.y, rp.inv_h[1], rp.nc[1]);
   const int cz = cell_coord(x.z, rp.inv_h[2], rp.nc[2]);
   float4 o;
-  o.x = frame_offset(x.x, cell_centre(a, rp, 0, cx), rp.Lf[0], rp.L[0]);
-  o.y = frame_offset(x.y, cell_centre(a, rp, 1, cy), rp.Lf[1], rp.L[1]);
-  o.z = frame_offset(x.z, cell_centre(a, rp, 2, cz), rp.Lf[2], rp.L[2]);
+  o.x = frame_offset(x.x, cell_centre(a, rp, 0, cx), rp.cq[0], rp.Lf[0], rp.L[0]);
+  o.y = frame_offset(x.y, cell_centre(a, rp, 1, cy), rp.cq[1], rp.Lf[1], rp.L[1]);
+  o.z = frame_offset(x.z, cell_centre(a, rp, 2, cz), rp.cq[2], rp.Lf[2], rp.L[2]);
   // tags must be a permutation of 0..N-1 and types lie in [0, ntypes): both
   // index tables later, so out-of-range values are refused here
   const int32_t tg = a.tag[i], ty = a.type[i];

@@ -57,9 +57,6 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
   const uint64_t oixy = pack2(oi.x, oi.y);
   const int max_nb = a.max_nb;
   // the pair kernel's row layout: groups of Pp = 32 / Wp particles, tiles of
-  // Wp columns per particle; this lane owns RC = Wp / WB of the columns of its
-  // particle and puts its n-th hit in column n mod RC, tile n / RC
-  // the pair kernel's row layout: groups of Pp = 32 / Wp particles, tiles of
   // Wp entries per particle; the row's entry k sits in tile k / Wp, column k % Wp
   const int lwp = a.w_store_log2, Wp = 1 << lwp, Pp = 32 >> lwp;
   const int tcap = max_nb >> lwp;  // tiles a row region holds
@@ -79,10 +76,11 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
   // cells is sorted by x.  The particle's candidates in a run lie within
   //   |x_j - x_i| <= sqrt(r_list^2 + band - rho^2),
   // rho = its y-z distance to the run's row of cells; a run with rho^2 above
-  // r_list^2 + band holds none.  eps (far above the FP32 rounding of stage
-  // coordinates) keeps the windows conservative.
-  const float hy = rp.hf[1], hz = rp.hf[2];
-  const float eps = 1e-4f * fmaxf(rp.hf[0], fmaxf(hy, hz));
+  // r_list^2 + band holds none.  eps (far above the grid rounding of stage
+  // coordinates and the drift of the hq-spaced frame faces from the cell
+  // faces) keeps the windows conservative.
+  const float hy = rp.hq[1], hz = rp.hq[2];
+  const float eps = rp.weps;
   const float yb = oi.y - (float)(((hs.s >> 2) & 3) - 2) * hy;  // height above the home row's lower face
   const float zb = oi.z - (float)((hs.s >> 4) - 2) * hz;
   auto xs = [&](int slot) { return lds1(src.spos + 16u * (uint32_t)(slot + 1)); };

@@ -47,10 +47,20 @@ struct Rep {
   double h[3];        // L / nc
   double half_h[3];   // h / 2
   double inv_h[3];    // nc / L
-  float hf[3];        // float(h): shift of a neighbouring cell's frame
+  // Stage frame (brick.cuh): FP32 offsets and stage coordinates are exact
+  // multiples of the grid gq (a power of two), frame cells are hq apart (h
+  // rounded to a multiple of 2 gq) and a periodic image shifts by wq (L - nc hq
+  // rounded to gq).  Every stage coordinate and every separation is then an
+  // exactly computed FP32 number: x_i - x_j seen from i's brick is exactly
+  // minus x_j - x_i seen from j's, so pair forces are exactly antisymmetric.
+  float hq[3];
+  float gq[3];
+  float wq[3];
+  float cq[3];        // 1.5 2^23 gq: the frame centres in ctab are shifted down by it
+  float weps;         // slack of the list build's x-windows (covers h - hq drift)
   float Lf[3];        // float(L)
   int64_t ctab0;      // first entry of the replica's cell-centre table (x, then y, then z)
-  float band;         // FP32 r^2 uncertainty band (see DESIGN: exact decisions)
+  float band;         // FP32 r^2 uncertainty band around r_list^2 and r_cut^2
   double volume;
 };
 
@@ -99,7 +109,7 @@ struct KArgs {
   float4 *vel4f;       // [cell-list position] FP32 velocity, tag bits in w (DPD)
   int32_t *cellpos;    // [particle] cell-list position
   int32_t *cell_rank;  // [cells] linear cell -> rank in brick order (per replica)
-  const double *ctab;  // cell centres (c + 1/2) h per replica and axis
+  const double *ctab;  // frame centres (c + 1/2) hq - cq per replica and axis (FP64)
   const int32_t *brick_stage;  // [bricks][64] cell slot of each stage cell (brick.cuh)
   const int4 *brick_info;      // [bricks] first cell slot, cell mask, replica
   const int32_t *brick_rep;    // [bricks] replica
@@ -176,20 +186,23 @@ __device__ __forceinline__ int cell_coord(double x, double inv_h, int nc) {
   return c < 0 ? 0 : c;
 }
 
-// FP32 offset of x from the centre ctr = (c + 1/2) h of its frame cell,
-// folded into (-L/2, L/2].  FP64 instructions are scarce on GB300 (a few per
-// clock per SM), so the centre comes from a table and the periodic fold
-// (needed only once the particle has crossed the box since its frame was
-// set) is decided on the FP32 value: the offsets stay below h + skin << L/2,
-// far from the fold's threshold.
-__device__ __forceinline__ float frame_offset(double x, double ctr, float Lf, double L) {
-  const double d = x - ctr;
-  const float df = (float)d;
-  if (fabsf(df) > 0.5f * Lf) return (float)(d + (df > 0.f ? -L : L));
-  return df;
+// FP32 offset of x from the centre (c + 1/2) hq of its frame cell c,
+// rounded once to the replica's grid gq (a power of two).  ctr_q is that
+// centre minus cq = 1.5 2^23 gq (exact in FP64): x - ctr_q lies in
+// [2^23 gq, 2^24 gq) while |offset| < 2^22 gq, and there the FP32 numbers are
+// exactly the multiples of gq, so the conversion rounds the offset to the
+// grid and subtracting cq is exact.  FP64 instructions are scarce on GB300
+// (a few per clock per SM), so the centre comes from a table and the periodic
+// fold (needed only once the particle has crossed the box since its frame
+// was set) is decided on the FP32 value: offsets stay below h + skin << L/2.
+__device__ __forceinline__ float frame_offset(double x, double ctr_q, float cq, float Lf, double L) {
+  const double d = x - ctr_q;
+  const float o = (float)d - cq;
+  if (fabsf(o) > 0.5f * Lf) return (float)(d + (o > 0.f ? -L : L)) - cq;
+  return o;
 }
 
-// Centre of cell c along axis ax of replica rp.
+// Frame centre of cell c along axis ax of replica rp, minus cq.
 __device__ __forceinline__ double cell_centre(const KArgs &a, const Rep &rp, int ax, int c) {
   const int off = ax == 0 ? 0 : ax == 1 ? rp.nc[0] : rp.nc[0] + rp.nc[1];
   return __ldg(a.ctab + rp.ctab0 + off + c);

@@ -119,6 +119,18 @@ __global__ void k_na_scatter(int64_t n, const int32_t *start, const int32_t *slo
   members[start[pcell[i]] + slot[i]] = (int32_t)i;
 }
 
+// Compensated (Neumaier) FP64 sum: the per-particle forces of a dense,
+// nearly cancelling neighbourhood stay within a few ulps of the exact sum.
+struct NSum {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double x) {
+    const double t = s + x;
+    c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return s + c; }
+};
+
 __global__ void k_na_forces(const double4 *pos, int64_t n, Grid g, double rc2, double lj1,
                             double lj2, double lj3, double lj4, const int32_t *count,
                             const int32_t *start, const int32_t *members, const int32_t *pcell,
@@ -128,7 +140,7 @@ __global__ void k_na_forces(const double4 *pos, int64_t n, Grid g, double rc2, d
   const double4 xi = pos[i];
   const int32_t c = pcell[i];
   const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
-  double f0 = 0, f1 = 0, f2 = 0, pe = 0;
+  NSum f0, f1, f2, pe;
   for (int s = 0; s < 27; s++) {
     int nx = (cx + s % 3 - 1 + g.nc[0]) % g.nc[0];
     int ny = (cy + (s / 3) % 3 - 1 + g.nc[1]) % g.nc[1];
@@ -144,16 +156,16 @@ __global__ void k_na_forces(const double4 *pos, int64_t n, Grid g, double rc2, d
       if (r2 >= rc2) continue;
       double r2i = 1.0 / r2, r6 = r2i * r2i * r2i;
       double fr = r2i * r6 * (lj1 * r6 - lj2);
-      f0 += fr * d[0];
-      f1 += fr * d[1];
-      f2 += fr * d[2];
-      pe += 0.5 * r6 * (lj3 * r6 - lj4);
+      f0.add(fr * d[0]);
+      f1.add(fr * d[1]);
+      f2.add(fr * d[2]);
+      pe.add(0.5 * r6 * (lj3 * r6 - lj4));
     }
   }
-  force[4 * i] = f0;
-  force[4 * i + 1] = f1;
-  force[4 * i + 2] = f2;
-  force[4 * i + 3] = pe;
+  force[4 * i] = f0.get();
+  force[4 * i + 1] = f1.get();
+  force[4 * i + 2] = f2.get();
+  force[4 * i + 3] = pe.get();
 }
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }

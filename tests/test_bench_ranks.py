@@ -76,3 +76,17 @@ def test_single_rank_needs_no_process_group():
         os.environ.update(env)
     assert bench.slowest_rank_time(1.5, None, "cpu") == 1.5
     assert bench.whole_job_rate(100, 10, 1, 2.0) == 500.0
+
+
+def test_timed_region_is_whole_graph_replays():
+    """The benchmark times whole graphs whatever --steps is: the graph length
+    divides the step count, and the untimed alignment leaves the step counter
+    on a graph (thermo) boundary."""
+    bench = _bench()
+    for steps, g in ((20, 20), (1000, 100), (150, 75), (7, 7), (101, 1), (300, 100), (1, 1)):
+        assert bench.graph_len(steps) == g
+        assert steps % g == 0 and g <= 100
+    for step in (0, 1, 99, 100, 1234):
+        for g in (1, 20, 100):
+            a = bench.align_steps(step + g, g)
+            assert (step + g + a) % g == 0 and 0 <= a < g

@@ -161,38 +161,54 @@ def test_bonds_after_sort_match_oracle(prec):
         assert rms <= 1e-5 and mx <= 1e-3, (rms, mx)
 
 
-def band_edge_state(seed, n_bg=700, n_pairs=400, L=20.0, r_cut=2.5, r_skin=0.3):
+def band_edge_state(seed, n_bg=500, n_pairs=64, L=20.0, r_cut=2.5, r_skin=0.3, d_min=0.9):
     """A dilute gas plus pairs whose squared separation lies within a few
-    FP64 ulps (and across the FP32 error band) of r_list^2 or r_cut^2.  Each
-    pair's first particle sits just inside a corner of a brick of 2 x 2 x 2
-    cells and its partner outside the brick along an outward diagonal, so the
-    partner's brick-frame FP32 coordinates are the largest a stage holds."""
+    FP64 ulps (and, for some, across the FP32 error band) of r_list^2 or
+    r_cut^2.  Each pair's first particle sits just inside a corner of a brick
+    of 2 x 2 x 2 cells and its partner outside the brick along an outward
+    diagonal, so the partner's brick-frame FP32 coordinates are the largest a
+    stage holds.  Every other separation is at least d_min (no overlaps, so
+    the mixed tolerance applies)."""
     rng = np.random.default_rng(seed)
     nc = math.floor(L / (r_cut + r_skin))
     h = L / nc
     nb = (nc + 1) // 2
-    pts = [rng.uniform(0.0, L, (n_bg, 3))]
-    for k in range(n_pairs):
+    pts = np.zeros((0, 3))
+
+    def far_from_all(x, skip=0):
+        if len(pts) - skip <= 0:
+            return True
+        d = pts[:len(pts) - skip] - x
+        d -= L * np.rint(d / L)
+        return np.min(np.einsum("ij,ij->i", d, d)) >= d_min * d_min
+
+    k = tries = 0
+    while k < n_pairs and tries < 50 * n_pairs:
+        tries += 1
         b = rng.integers(0, nb, 3)
         side = rng.integers(0, 2, 3)
         corner = np.minimum(2 * b + 2 * side, nc) * h
         sgn = np.where(side == 1, 1.0, -1.0)  # outward
-        a = corner - sgn * rng.uniform(0.005, 0.05, 3)
+        a = np.mod(corner - sgn * rng.uniform(0.005, 0.05, 3), L)
         u = sgn * rng.uniform(0.3, 1.0, 3)
         u /= np.linalg.norm(u)
         target = (r_cut + r_skin) if k % 2 == 0 else r_cut
-        ulps = int(rng.integers(-4, 5))
         if k % 8 == 1:  # also spread across the FP32 band, not only FP64 ulps
             r = target * (1.0 + rng.uniform(-3e-6, 3e-6))
         else:
-            r = target * (1.0 + ulps * 2.0 ** -52)
-        pts.append(np.stack([a, a + r * u]))
-    xyz = np.mod(np.concatenate(pts), L)
-    n = len(xyz)
+            r = target * (1.0 + int(rng.integers(-4, 5)) * 2.0 ** -52)
+        c = np.mod(a + r * u, L)
+        if far_from_all(a) and far_from_all(c):
+            pts = np.concatenate([pts, a[None], c[None]])
+            k += 1
+    while len(pts) < 2 * n_pairs + n_bg:
+        x = rng.uniform(0.0, L, 3)
+        if far_from_all(x):
+            pts = np.concatenate([pts, x[None]])
+    n = len(pts)
     pos = np.zeros((n, 4))
-    pos[:, :3] = xyz
-    vel = np.zeros((n, 4))
-    return inputs.State(pos=pos, vel=vel, image=np.zeros((n, 4), np.int32),
+    pos[:, :3] = pts
+    return inputs.State(pos=pos, vel=np.zeros((n, 4)), image=np.zeros((n, 4), np.int32),
                         tag=np.arange(n, dtype=np.int32), type=np.zeros(n, np.int32),
                         box=np.array([[L, L, L]]), offsets=np.array([0, n], np.int64))
 
@@ -201,10 +217,10 @@ def band_edge_state(seed, n_bg=700, n_pairs=400, L=20.0, r_cut=2.5, r_skin=0.3):
 def test_band_edge_pairs_rows_and_forces_exact(w):
     st = band_edge_state(seed=70 + w)
     L = st.box[0]
-    cb, rb = oracle.neighbors(st.pos, L, 2.8, max_nb=64, method="brute")
+    cb, rb = oracle.neighbors(st.pos, L, 2.8, max_nb=128, method="brute")
     ref, _, absf = oracle.lj_forces(st.pos, L, 2.5)
     for prec in ("fp64", "mixed"):
-        s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, precision=prec, max_nb=64)
+        s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, precision=prec, max_nb=128)
         s.set_tuning(md.KERNEL_PAIR, 128, w)
         s.set_tuning(md.KERNEL_NLIST, 64, w)
         s.prepare()

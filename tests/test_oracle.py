@@ -438,13 +438,13 @@ def test_hilbert_is_a_unit_step_bijection(bits):
 
 def test_sfc_order_is_permutation_walking_adjacent_bricks():
     L = 24.0
-    nc = 8  # r_list 3.0 -> 8 cells of width 3, 4 bricks of 2 x 2 x 2 cells per edge
+    nc = 8  # r_list 2.99 -> 8 cells of width 3, 4 bricks of 2 x 2 x 2 cells per edge
     cells = np.array([(x, y, z) for x in range(nc) for y in range(nc) for z in range(nc)])
     rng = np.random.default_rng(2)
     perm = rng.permutation(len(cells))
     pos = np.zeros((len(cells), 4))
     pos[:, :3] = (cells[perm] + 0.5) * 3.0
-    order = oracle.sfc_order(pos, L, 3.0)
+    order = oracle.sfc_order(pos, L, 2.99)
     assert sorted(order.tolist()) == list(range(len(cells)))
     walk = cells[perm][order]
     bricks = walk // 2
@@ -461,7 +461,7 @@ def test_sfc_order_is_permutation_walking_adjacent_bricks():
 def test_sfc_order_odd_grid_and_many_per_cell():
     # 7 cells per edge (the last brick layer is one cell thick), several
     # particles per cell: bricks form contiguous runs along a unit-step walk
-    L, rl = 21.0, 3.0
+    L, rl = 21.0, 2.99
     rng = np.random.default_rng(4)
     pos = np.zeros((3000, 4))
     pos[:, :3] = rng.uniform(0.0, L, (3000, 3))
@@ -497,3 +497,22 @@ def test_local_neighbourhood_answers_equal_whole_system_ones():
         d = np.linalg.norm(f[k, :3] - fr[i, :3])
         assert d <= 1e-12 * max(np.linalg.norm(fr[i, :3]), 1e-2 * afr[i]), int(i)
     assert np.allclose(absf, afr[samples], rtol=1e-12)
+
+
+def test_cell_list_rows_in_a_box_that_is_an_exact_multiple_of_r_list():
+    """Box 12 = 4 r_list: the cell list uses 3 cells (the 1e-12 margin), and
+    pairs straddling the planes x = k r_list at r_list (1 - 1e-14) are rows of
+    each other, as brute force says."""
+    L, rl = 12.0, 3.0
+    assert oracle.cells_per_dim(L, rl) == 3
+    d = rl * (1 - 1e-14)
+    pos = np.zeros((8, 4))
+    yz = ((0.5, 0.5), (6.5, 0.5), (0.5, 6.5), (6.5, 6.5))
+    for k, x0 in enumerate((3.0, 6.0, 9.0, 12.0)):
+        pos[2 * k, :3] = [x0 - 0.5 * d, *yz[k]]
+        pos[2 * k + 1, :3] = [x0 + 0.5 * d, *yz[k]]
+    pos[:, :3] = np.mod(pos[:, :3], L)
+    cb, rb = oracle.neighbors(pos, L, rl, method="brute")
+    cc, rc = oracle.neighbors(pos, L, rl, method="cells")
+    assert cb.tolist() == [1] * 8
+    assert np.array_equal(cb, cc) and np.array_equal(rb, rc)
