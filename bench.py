@@ -356,6 +356,31 @@ def force_error(f, ref, absf):
 # --------------------------------------------------------------------------
 # the forms beside the headline
 
+def fp64_peak(stream, torch):
+    """Measured FP64 rate (DFMA chains filling every SM; best of 5 launches,
+    CUDA events on the launching stream), TFLOP/s."""
+    import ctypes as C
+    from paper_1412_3387_gb300 import build as _b
+    lib = C.CDLL(_b.RATE_LIB)
+    lib.mdrate_dfma.restype = C.c_double
+    lib.mdrate_dfma.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = nsm * 8
+    out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    best = 0.0
+    for _ in range(6):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = lib.mdrate_dfma(C.c_void_p(out.data_ptr()), blocks, 200, C.c_void_p(stream.cuda_stream))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if flops < 0:
+            return None
+        best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
 def lj_error_subrun(md, dev, stream):
     """Mixed and FP64 force errors against the oracle on the 65,536-particle
     sub-run of the headline fluid: a jittered fcc start advanced 200 steps by
@@ -669,12 +694,49 @@ def main():
             ready_for_graphs(s64, g64, stream, torch)
             t64 = time_run(s64, args.fp64_steps, stream, torch)
             s64.check_error()
+            ms64 = pair_launch_ms(s64, stream, torch, 5)
+            peak64 = fp64_peak(stream, torch)
+            # FP64 pair kernel: bound by the FP64 pipe.  Per pair inside r_cut
+            # it issues about 40 FP64 instructions (the exact minimum-image
+            # distance: 3 sub, 3 mul, 3 round, 3 mul, 3 sub, 3 mul, 2 add; the
+            # LJ force: the reciprocal ~ 8, 2 mul for r^-6, 4 for the magnitude,
+            # 3 mul and 3 add for the components); each occupies the pipe like
+            # one DFMA, counted as 2 FLOPs against the DFMA peak.  55.3 pairs
+            # per particle inside r_cut at this density.
+            fl = 2.0 * 40.0 * 55.3 * args.n / (ms64 * 1e-3) / 1e12
             forms["fp64"] = {"value": args.n * args.fp64_steps / t64,
                              "ms_per_step": 1e3 * t64 / args.fp64_steps, "steps": args.fp64_steps,
-                             "graph_steps_used": g64,
-                             "pair_ms_per_launch": pair_launch_ms(s64, stream, torch, 5)}
+                             "graph_steps_used": g64, "pair_ms_per_launch": ms64,
+                             "pair_roofline": {"kernel": "k_pair<LJ, FP64>", "bound": "fp64",
+                                               "achieved": fl, "peak": peak64, "unit": "TFLOP/s",
+                                               "frac": fl / peak64 if peak64 else None,
+                                               "peak_source": "measured (DFMA chains, this run)",
+                                               "fp64_instructions_per_pair": 40.0,
+                                               "pairs_per_particle": 55.3}}
             s64.close()
             del s64
+            torch.cuda.empty_cache()
+        if want("nvt"):
+            # the same fluid under a Nose-Hoover thermostat (the ensemble of the
+            # paper's weak-scaling benchmark: one kinetic-energy sum per step)
+            stn = st.copy()
+            for k in ("pos", "vel", "image", "tag", "type"):
+                setattr(stn, k, eq_state[k])
+            gn = graph_len(args.fp64_steps)
+            sn = md.MDSystem(stn, precision="mixed", stream=stream, max_nb=max_nb,
+                             **dict(common, thermo_period=gn, graph_steps=gn))
+            for kern, name in ((md.KERNEL_PAIR, "pair"), (md.KERNEL_NLIST, "nlist")):
+                sn.set_tuning(kern, *tune_used[name])
+            sn.set_integrator("nose-hoover", kT=H["T"], param=0.5)
+            ready_for_graphs(sn, gn, stream, torch)
+            tn = time_run(sn, args.fp64_steps, stream, torch)
+            sn.check_error()
+            forms["nvt_nose_hoover"] = {"value": args.n * args.fp64_steps / tn,
+                                        "ms_per_step": 1e3 * tn / args.fp64_steps,
+                                        "steps": args.fp64_steps, "graph_steps_used": gn,
+                                        "kT": H["T"], "tau": 0.5}
+            sn.close()
+            del sn
             torch.cuda.empty_cache()
         if want("errors"):
             forms["error_vs_oracle_64k"] = lj_error_subrun(md, dev, stream)

@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 2
+#define MD_ABI_VERSION 3
 
 typedef struct md_system md_system;
 typedef struct CUstream_st *md_stream; /* a cudaStream_t; NULL = legacy default stream */
@@ -61,6 +61,7 @@ typedef enum {
 typedef enum { MD_FP64 = 0, MD_MIXED = 1 } md_precision;
 typedef enum { MD_PAIR_LJ = 0, MD_PAIR_DPD = 1 } md_pair_kind;
 typedef enum { MD_KERNEL_NLIST = 0, MD_KERNEL_PAIR = 1 } md_kernel;
+typedef enum { MD_NVE = 0, MD_LANGEVIN = 1, MD_NOSE_HOOVER = 2 } md_integrator;
 
 /* Caller-owned particle state, all DEVICE arrays of N = n_total entries,
  * concatenated over replicas (replica r owns [replica_offset[r],
@@ -217,6 +218,39 @@ md_status md_reduce_thermo(md_system *s, double *dev_out, md_stream stream);
  * non-finite position or an over-full cell, list builds are skipped (the
  * steps' results are invalid; md_poll_error reports the error). */
 md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream stream);
+
+/* Integrator (Sec. 3 lists NVE, NVT with the Martyna-Tobias-Klein update
+ * equations, and Langevin dynamics; Sec. 6.1 runs NVT with a Nose-Hoover
+ * thermostat that sums the kinetic energy once per step).  Default MD_NVE.
+ *   MD_NVE          velocity Verlet; kT, param, seed unused.
+ *   MD_LANGEVIN     BAOAB splitting with friction gamma = param >= 0:
+ *                   v += dt/2 F/m; x += dt/2 v; v = c v + sqrt((1 - c^2) kT/m)
+ *                   theta; x += dt/2 v; [forces]; v += dt/2 F/m, c =
+ *                   exp(-gamma dt); theta = sqrt(3) (2u - 1) per component,
+ *                   u from words 0..2 of Philox-4x32-10 with counter (tag,
+ *                   0xFFFFFFFF, step lo, step hi) and key (seed lo, seed hi),
+ *                   step = the time step being computed.
+ *   MD_NOSE_HOOVER  one Nose-Hoover thermostat per replica, period tau =
+ *                   param > 0, in the Trotter splitting exp(iL_T dt/2)
+ *                   exp(iL_v dt/2) exp(iL_x dt) exp(iL_v dt/2) exp(iL_T dt/2);
+ *                   each thermostat half step, with g = 3N - 3 and G =
+ *                   (2 KE / g) / kT - 1: xi += dt/4 G / tau^2; v *= exp(-xi
+ *                   dt/2); eta += xi dt/2; xi += dt/4 G' / tau^2 (G' after the
+ *                   scaling).  The kinetic energy is summed once per step, in
+ *                   the second half-kick; the resulting velocity scales are
+ *                   applied by the next first half (md_integrate(1)), and by
+ *                   md_step / md_run before they return.  Conserved:
+ *                   KE + PE + g kT tau^2 xi^2 / 2 + g kT eta.
+ * Resets the thermostat state (xi = eta = 0); the next step computes its
+ * first half step from the velocities at that time (call this again after
+ * writing velocities directly).  Not valid with DPD pair forces (their
+ * noise and friction are the thermostat).  Errors: MD_ERR_INVALID_ARG. */
+md_status md_set_integrator(md_system *s, int32_t kind, double kT, double param,
+                            uint64_t seed);
+
+/* Nose-Hoover state between steps (after the last completed step's end half
+ * step), HOST [R][2] = (xi, eta) per replica.  Synchronises. */
+md_status md_get_thermostat(md_system *s, double *host_out);
 
 /* Autotuner (Sec. 5.2): for the pair and neighbour-list kernels, times every
  * (block size b = 32 k <= 512, threads per particle w = 2^m <= 32) pair with

@@ -48,7 +48,9 @@ class Params(C.Structure):
         ("coeff", C.c_void_p), ("shift_energy", C.c_int32),
         ("thermo_period", C.c_int32), ("K", C.c_double), ("r0", C.c_double),
         ("n_bonds", C.c_int64), ("bonds", C.c_void_p), ("step0", C.c_int64),
-        ("max_nb", C.c_int32),
+        ("max_nb", C.c_int32), ("integrator", C.c_int32), ("t_kT", C.c_double),
+        ("t_gamma", C.c_double), ("t_tau", C.c_double), ("t_seed", C.c_uint64),
+        ("nh_state", C.c_void_p),
     ]
 
 
@@ -79,6 +81,9 @@ def lib():
                 "orc_hilbert3": (U64, [U32, U32, U32, I32]),
                 "orc_sfc_order": (None, [I64, P, P, D, P]),
                 "orc_run": (I64, [I64, P, P, P, P, P, P, C.POINTER(Params), I64, P]),
+                "orc_langevin_noise": (None, [I32, U64, U64, P]),
+                "orc_baoab_first": (None, [I64, P, P, P, P, P, D, D, D, D, U64, U64, P]),
+                "orc_nh_half": (D, [I64, P, D, D, D, D, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -256,11 +261,42 @@ def sfc_order(pos, L, r_list):
     return order
 
 
+def langevin_noise(tag, step, seed):
+    out = np.zeros(3)
+    lib().orc_langevin_noise(int(tag), int(step), int(seed), _p(out))
+    return out
+
+
+def baoab_first(pos, vel, image, force, tag, dt, gamma, kT, step, seed, L, mass=1.0):
+    pos, vel, force = _f64(pos).copy(), _f64(vel).copy(), _f64(force)
+    image, tag = _i32(image).copy(), _i32(tag)
+    lib().orc_baoab_first(pos.shape[0], _p(pos), _p(vel), _p(image), _p(force), _p(tag),
+                          float(dt), float(mass), float(gamma), float(kT), int(step), int(seed),
+                          _p(_box(L)))
+    return pos, vel, image
+
+
+def nh_half(vel, kT, tau, dt, state, mass=1.0):
+    """One Nose-Hoover half step on a copy of vel; state = [xi, eta] is
+    updated in place.  Returns (vel, scale)."""
+    vel = _f64(vel).copy()
+    st = np.ascontiguousarray(state, np.float64)
+    s = lib().orc_nh_half(vel.shape[0], _p(vel), float(mass), float(kT), float(tau), float(dt),
+                          _p(st))
+    state[:] = st
+    return vel, s
+
+
+INTEGRATORS = {"nve": 0, "langevin": 1, "nose-hoover": 2}
+
+
 def run(pos, vel, image, L, n_steps, *, r_cut, r_skin, dt, pair="lj", type=None,
         tag=None, coeff=((1.0, 1.0),), kT=1.0, seed=0, mass=1.0, shift_energy=False,
-        thermo_period=0, bonds=None, K=0.0, r0=0.0, step0=0, max_nb=256):
+        thermo_period=0, bonds=None, K=0.0, r0=0.0, step0=0, max_nb=256,
+        integrator="nve", t_kT=1.0, gamma=1.0, tau=1.0, t_seed=0, nh_state=None):
     """Full MD loop on copies of the inputs; returns a dict with the final
-    state, forces, thermo rows and the number of list builds."""
+    state, forces, thermo rows, the number of list builds and (Nose-Hoover)
+    the thermostat state [xi, eta] (nh_state gives its initial value)."""
     pos, vel = _f64(pos).copy(), _f64(vel).copy()
     image = _i32(image).copy()
     n = pos.shape[0]
@@ -284,6 +320,10 @@ def run(pos, vel, image, L, n_steps, *, r_cut, r_skin, dt, pair="lj", type=None,
     p.bonds = b.ctypes.data if b.shape[0] else None
     p.step0 = int(step0)
     p.max_nb = int(max_nb)
+    p.integrator = INTEGRATORS[integrator]
+    p.t_kT, p.t_gamma, p.t_tau, p.t_seed = float(t_kT), float(gamma), float(tau), int(t_seed)
+    nh = np.ascontiguousarray(np.zeros(2) if nh_state is None else nh_state, np.float64).copy()
+    p.nh_state = nh.ctypes.data
     n_th = (n_steps // thermo_period + 1) if thermo_period else 0
     th = np.zeros((max(n_th, 1), 8))
     builds = lib().orc_run(n, _p(pos), _p(vel), _p(image), _p(t), _p(g), _p(force),
@@ -293,4 +333,4 @@ def run(pos, vel, image, L, n_steps, *, r_cut, r_skin, dt, pair="lj", type=None,
     rows = th[: (sum(1 for s in range(step0 + 1, step0 + n_steps + 1)
                      if thermo_period and s % thermo_period == 0))]
     return dict(pos=pos, vel=vel, image=image, force=force, thermo=rows,
-                builds=int(builds))
+                builds=int(builds), nh_state=nh)

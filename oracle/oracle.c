@@ -443,6 +443,67 @@ void orc_vv_second(int64_t n, double *vel, const double *force, double dt,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Thermostats (Sec. 3: NVT with the Martyna-Tobias-Klein update equations,
+ * Langevin dynamics; Sec. 6.1 runs NVT with a Nose-Hoover thermostat that
+ * needs one kinetic-energy sum per step).                                  */
+
+void orc_langevin_noise(int32_t tag, uint64_t step, uint64_t seed, double *theta) {
+    uint32_t ctr[4] = {(uint32_t)tag, 0xFFFFFFFFu, (uint32_t)step, (uint32_t)(step >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    for (int k = 0; k < 3; k++) {
+        double u = ((double)w[k] + 0.5) * 0x1p-32;
+        theta[k] = sqrt(3.0) * (2.0 * u - 1.0);
+    }
+}
+
+void orc_baoab_first(int64_t n, double *pos, double *vel, int32_t *image,
+                     const double *force, const int32_t *tag, double dt,
+                     double mass, double gamma, double kT, uint64_t step,
+                     uint64_t seed, const double *L) {
+    double h = 0.5 * dt / mass;
+    double c = exp(-gamma * dt);
+    double sigma = sqrt((1.0 - c * c) * kT / mass);
+    for (int64_t i = 0; i < n; i++) {
+        double theta[3];
+        orc_langevin_noise(tag[i], step, seed, theta);
+        for (int k = 0; k < 3; k++) {
+            double v = vel[4 * i + k] + h * force[4 * i + k];   /* B */
+            double x = pos[4 * i + k] + 0.5 * dt * v;           /* A */
+            v = c * v + sigma * theta[k];                       /* O */
+            x = x + 0.5 * dt * v;                               /* A */
+            int32_t img = image[4 * i + k];
+            while (x >= L[k]) { x -= L[k]; img++; }
+            while (x < 0.0) { x += L[k]; img--; }
+            if (x >= L[k]) { x -= L[k]; img++; }
+            vel[4 * i + k] = v;
+            pos[4 * i + k] = x;
+            image[4 * i + k] = img;
+        }
+    }
+}
+
+double orc_nh_half(int64_t n, double *vel, double mass, double kT, double tau,
+                   double dt, double *state) {
+    acc_t ke = {0, 0};
+    for (int64_t i = 0; i < n; i++) {
+        const double *v = vel + 4 * i;
+        acc_add(&ke, 0.5 * mass * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+    }
+    double g = 3.0 * (double)n - 3.0;
+    double KE = acc_get(&ke);
+    state[0] += 0.25 * dt * ((2.0 * KE / g) / kT - 1.0) / (tau * tau);
+    double s = exp(-0.5 * dt * state[0]);
+    for (int64_t i = 0; i < n; i++)
+        for (int k = 0; k < 3; k++) vel[4 * i + k] *= s;
+    state[1] += 0.5 * dt * state[0];
+    KE *= s * s;
+    state[0] += 0.25 * dt * ((2.0 * KE / g) / kT - 1.0) / (tau * tau);
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Thermodynamic reductions (Sec. 4.3.3: kinetic energy, virial etc. grouped
  * into one global synchronization per step).                               */
 
@@ -579,11 +640,18 @@ int64_t orc_run(int64_t n, double *pos, double *vel, int32_t *image,
         builds++;                                                              \
     } while (0)
 
+    double nh_local[2] = {0.0, 0.0};
+    double *nh = p->nh_state ? p->nh_state : nh_local;
     ORC_BUILD();
     compute_forces(n, pos, vel, type, tag, p, p->step0, counts, rows, force, virial);
     for (int64_t s = 1; s <= n_steps; s++) {
         uint64_t t = (uint64_t)(p->step0 + s);
-        orc_vv_first(n, pos, vel, image, force, p->dt, p->mass, p->L);
+        if (p->integrator == 2) orc_nh_half(n, vel, p->mass, p->t_kT, p->t_tau, p->dt, nh);
+        if (p->integrator == 1)
+            orc_baoab_first(n, pos, vel, image, force, tag, p->dt, p->mass, p->t_gamma,
+                            p->t_kT, t, p->t_seed, p->L);
+        else
+            orc_vv_first(n, pos, vel, image, force, p->dt, p->mass, p->L);
         int rebuild = 0;
         for (int64_t i = 0; i < n && !rebuild; i++) {
             double d[3];
@@ -592,6 +660,7 @@ int64_t orc_run(int64_t n, double *pos, double *vel, int32_t *image,
         if (rebuild) ORC_BUILD();
         compute_forces(n, pos, vel, type, tag, p, t, counts, rows, force, virial);
         orc_vv_second(n, vel, force, p->dt, p->mass);
+        if (p->integrator == 2) orc_nh_half(n, vel, p->mass, p->t_kT, p->t_tau, p->dt, nh);
         if (p->thermo_period > 0 && t % (uint64_t)p->thermo_period == 0 && thermo_out) {
             orc_thermo(n, vel, force, virial, p->mass, p->L, thermo_out + 8 * n_out);
             n_out++;

@@ -138,6 +138,30 @@ uint64_t orc_hilbert3(uint32_t x, uint32_t y, uint32_t z, int32_t bits);
 void orc_sfc_order(int64_t n, const double *pos, const double *L, double r_list,
                    int32_t *order);
 
+/* Langevin noise of one particle and step: theta_k = sqrt(3) (2 u_k - 1),
+ * u_k = (w_k + 1/2) 2^-32 (k = 0, 1, 2), words 0..2 of Philox-4x32-10 with
+ * counter (tag, 0xFFFFFFFF, step lo, step hi) and key (seed lo, seed hi).
+ * Unit variance, mean zero. */
+void orc_langevin_noise(int32_t tag, uint64_t step, uint64_t seed, double *theta);
+
+/* Langevin dynamics, BAOAB splitting (Leimkuhler & Matthews 2013), first
+ * part of a step: v += dt/2 F/m; x += dt/2 v; v = c v + sqrt((1 - c^2) kT/m)
+ * theta (c = exp(-gamma dt)); x += dt/2 v; wrap into [0, L) counting images.
+ * The step's last part is orc_vv_second (v += dt/2 F/m). */
+void orc_baoab_first(int64_t n, double *pos, double *vel, int32_t *image,
+                     const double *force, const int32_t *tag, double dt,
+                     double mass, double gamma, double kT, uint64_t step,
+                     uint64_t seed, const double *L);
+
+/* Half a step of one Nose-Hoover thermostat of period tau (the Trotter
+ * factor exp(iL_T dt/2) of Martyna, Tuckerman, Tobias & Klein 1996 with one
+ * thermostat): with g = 3N - 3 degrees of freedom, G = (2 KE / g) / kT - 1,
+ *   xi += dt/4 G / tau^2;  s = exp(-xi dt/2);  v *= s;  eta += xi dt/2;
+ *   xi += dt/4 G' / tau^2 (G' with the scaled KE).
+ * state = {xi, eta}.  Returns the scale s applied to the velocities. */
+double orc_nh_half(int64_t n, double *vel, double mass, double kT, double tau,
+                   double dt, double *state);
+
 typedef struct {
     double L[3];
     double r_cut, r_skin, dt, mass, kT;
@@ -152,11 +176,19 @@ typedef struct {
     const int32_t *bonds;  /* index pairs */
     int64_t step0;         /* time step of the initial state */
     int32_t max_nb;
+    int32_t integrator;    /* 0 = NVE velocity Verlet, 1 = Langevin (BAOAB),
+                              2 = Nose-Hoover (one thermostat, MTK splitting) */
+    double t_kT;           /* thermostat temperature */
+    double t_gamma;        /* Langevin friction */
+    double t_tau;          /* Nose-Hoover period */
+    uint64_t t_seed;       /* Langevin noise key */
+    double *nh_state;      /* Nose-Hoover {xi, eta}, updated in place (or NULL) */
 } orc_params;
 
-/* Whole MD loop: forces at step0, then n_steps velocity-Verlet steps with a
- * Verlet list rebuilt when any particle moved more than r_skin/2 since the
- * last build.  thermo_out receives 8 doubles (orc_thermo) at every step t
+/* Whole MD loop: forces at step0, then n_steps steps of the chosen
+ * integrator (velocity Verlet, BAOAB Langevin, or velocity Verlet between
+ * two Nose-Hoover half steps) with a Verlet list rebuilt when any particle
+ * moved more than r_skin/2 since the last build.  thermo_out receives 8 doubles (orc_thermo) at every step t
  * with t % thermo_period == 0, t > step0.  force holds the final forces.
  * Returns the number of neighbour-list builds, or -1 on row overflow. */
 int64_t orc_run(int64_t n, double *pos, double *vel, int32_t *image,

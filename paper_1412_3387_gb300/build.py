@@ -17,6 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmdgb.so")
+RATE_LIB = os.path.join(BUILD, "libmdrate.so")  # FP64 rate microbenchmark (not the MD ABI)
 SOURCES = ["api.cu", "k_cells.cu", "k_nlist.cu", "k_pair.cu", "k_pair_lj_mixed.cu",
            "k_pair_lj_fp64.cu", "k_pair_dpd_mixed.cu", "k_pair_dpd_fp64.cu", "k_integrate.cu",
            "noalloc.cu"]
@@ -64,8 +65,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             os.replace(o + ".tmp", o)
         return o
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        objs = list(ex.map(compile_one, SOURCES + ["fp64_rate.cu"]))
+    rate_obj = objs.pop()
+    if force or _stale(RATE_LIB, [rate_obj]):
+        tmp = RATE_LIB + f".{os.getpid()}.tmp"
+        r = subprocess.run([cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, rate_obj,
+                            "-Xlinker", "-rpath,/usr/local/cuda/lib64"], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, RATE_LIB)
     if force or _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
         cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,

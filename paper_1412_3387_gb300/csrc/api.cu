@@ -36,6 +36,9 @@ struct md_system {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool gvalid = false;
+  // Nose-Hoover: the start-of-step thermostat scale has been computed for the
+  // current velocities
+  bool nh_primed = false;
 };
 
 namespace {
@@ -93,7 +96,8 @@ struct Plan {
       o_brick_rep, o_brick_desc, o_cell_count, o_cell_start,
       o_chunk_sum, o_cell_idx, o_cellpos, o_pcell, o_pslot, o_n_nb, o_rtag, o_pos4f, o_oref, o_vel4f,
       o_nl, o_nl_tiles, o_force, o_virial, o_tpart, o_ds, o_rebuild, o_sort_now, o_last_sort, o_ident,
-      o_list_ok, o_coeff, o_btab, o_s_pos, o_s_vel, o_s_img, o_s_tag, o_s_type, o_s_oref;
+      o_list_ok, o_coeff, o_btab, o_s_pos, o_s_vel, o_s_img, o_s_tag, o_s_type, o_s_oref, o_nh,
+      o_nh_part;
   size_t total = 0;
 };
 
@@ -275,6 +279,8 @@ md_status make_plan(const md_params *p, Plan &pl) {
   pl.o_s_tag = take(sizeof(int32_t) * N);
   pl.o_s_type = take(sizeof(int32_t) * N);
   pl.o_s_oref = take(sizeof(float4) * N);
+  pl.o_nh = take(sizeof(double) * kNhFields * R);
+  pl.o_nh_part = take(sizeof(double) * (size_t)pl.n_tchunks);
   pl.total = o;
   return MD_OK;
 }
@@ -288,6 +294,12 @@ T *at(void *base, size_t off) { return reinterpret_cast<T *>(static_cast<char *>
 md_status enqueue_step(md_system *s, int want_virial, cudaStream_t st, bool fold_in = false,
                        bool close = true) {
   const KArgs &a = s->a;
+  if (a.integ == MD_NOSE_HOOVER) {
+    // the thermostat needs every step's second half-kick (its kinetic-energy
+    // sum lives there): no folding
+    fold_in = false;
+    close = true;
+  }
   MD_CUDA(launch_integrate1(a, st, fold_in));
   MD_CUDA(launch_bin(a, 0, st));
   if (s->p.sort_period > 0) MD_CUDA(launch_sort(a, 0, st));
@@ -314,6 +326,14 @@ void set_pair_w(md_system *s, Launch l) {
   s->tune[MD_KERNEL_PAIR] = l;
   s->a.w_store_log2 = ilog2(l.w);
   s->gvalid = false;
+}
+
+// Nose-Hoover: the first step of a sequence needs the thermostat's
+// start-of-step half step from the current velocities.
+cudaError_t nh_prime(md_system *s, cudaStream_t st) {
+  if (s->a.integ != MD_NOSE_HOOVER || s->nh_primed) return cudaSuccess;
+  s->nh_primed = true;
+  return launch_nh_begin(s->a, st);
 }
 
 bool valid_launch(int block, int w) {
@@ -462,6 +482,12 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   a.s_type = at<int32_t>(ws, pl.o_s_type);
   a.s_oref = at<float4>(ws, pl.o_s_oref);
   a.coeff = at<void>(ws, pl.o_coeff);
+  a.nh = at<double>(ws, pl.o_nh);
+  a.nh_part = at<double>(ws, pl.o_nh_part);
+  a.integ = MD_NVE;
+  a.t_kT = 1.0;
+  a.t_c = 1.0;
+  a.t_tau = 1.0;
   a.max_nb = pl.max_nb;
   a.sort_period = p->sort_period;
   a.max_bonds = p->max_bonds;
@@ -608,6 +634,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
       cudaMemsetAsync(at<void>(ws, pl.o_btab), 0xff, sizeof(int32_t) * (size_t)p->max_bonds * pl.n, stream))
     return fail(MD_ERR_CUDA);
   if (launch_init_frames(a, stream) != cudaSuccess) return fail(MD_ERR_CUDA);
+  if (launch_nh_reset(a, stream) != cudaSuccess) return fail(MD_ERR_CUDA);
   if (cudaStreamSynchronize(stream) != cudaSuccess) return fail(MD_ERR_CUDA);
   uint32_t err = 0;
   if (cudaMemcpy(&err, &a.ds->error, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -710,11 +737,13 @@ md_status md_integrate(md_system *s, int32_t half, md_stream stream) {
   if (!s || (half != 1 && half != 2)) return MD_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (half == 1) {
+    MD_CUDA(nh_prime(s, st));
     MD_CUDA(launch_integrate1(s->a, st));
     s->bin_all = s->bin_cond = false;
     s->step++;
   } else {
     MD_CUDA(launch_integrate2(s->a, st));
+    if (s->a.integ == MD_NOSE_HOOVER) s->nh_primed = true;
   }
   return MD_OK;
 }
@@ -724,9 +753,11 @@ md_status md_step(md_system *s, int32_t want_virial, md_stream stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   md_status e = prepare(s, st);
   if (e != MD_OK) return e;
+  MD_CUDA(nh_prime(s, st));
   e = enqueue_step(s, want_virial ? 1 : 0, st);
   s->bin_all = s->bin_cond = false;
   if (e == MD_OK) s->step++;
+  if (e == MD_OK && s->a.integ == MD_NOSE_HOOVER) MD_CUDA(launch_nh_flush(s->a, st));
   return e;
 }
 
@@ -746,6 +777,7 @@ md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream st
   const int64_t rows = period > 0 ? (s->step + n_steps) / period - s->step / period : 0;
   MD_CUDA(launch_run_begin(s->a, thermo_out, period, rows, st));
   if (n_steps > 0) s->bin_all = s->bin_cond = false;
+  if (n_steps > 0) MD_CUDA(nh_prime(s, st));
   int64_t left = n_steps;
   while (left > 0) {
     if (gsteps > 0 && left >= gsteps && (period == 0 || s->step % period == 0)) {
@@ -783,6 +815,45 @@ md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream st
       s->step++;
       left--;
     }
+  }
+  // Nose-Hoover: leave full-step velocities (the end-of-step scale applied)
+  if (n_steps > 0 && s->a.integ == MD_NOSE_HOOVER) MD_CUDA(launch_nh_flush(s->a, st));
+  return MD_OK;
+}
+
+md_status md_set_integrator(md_system *s, int32_t kind, double kT, double param, uint64_t seed) {
+  if (!s) return MD_ERR_INVALID_ARG;
+  if (kind != MD_NVE && kind != MD_LANGEVIN && kind != MD_NOSE_HOOVER) return MD_ERR_INVALID_ARG;
+  if (kind != MD_NVE) {
+    if (s->p.pair == MD_PAIR_DPD) return MD_ERR_INVALID_ARG;
+    if (!(kT > 0) || !std::isfinite(kT) || !std::isfinite(param)) return MD_ERR_INVALID_ARG;
+    if (kind == MD_LANGEVIN && !(param >= 0)) return MD_ERR_INVALID_ARG;
+    if (kind == MD_NOSE_HOOVER && !(param > 0)) return MD_ERR_INVALID_ARG;
+  }
+  KArgs &a = s->a;
+  a.integ = kind;
+  a.t_kT = kind == MD_NVE ? 1.0 : kT;
+  a.t_seed = seed;
+  a.t_tau = kind == MD_NOSE_HOOVER ? param : 1.0;
+  a.t_c = kind == MD_LANGEVIN ? std::exp(-param * a.dt) : 1.0;
+  a.t_sig = kind == MD_LANGEVIN ? std::sqrt((1.0 - a.t_c * a.t_c) * kT / a.mass) : 0.0;
+  std::vector<double> nh(kNhFields * (size_t)a.R, 0.0);
+  for (int r = 0; r < a.R; r++) nh[kNhFields * r + 2] = nh[kNhFields * r + 3] = 1.0;
+  MD_CUDA(cudaDeviceSynchronize());
+  MD_CUDA(cudaMemcpy(a.nh, nh.data(), sizeof(double) * nh.size(), cudaMemcpyHostToDevice));
+  s->nh_primed = false;
+  s->gvalid = false;
+  return MD_OK;
+}
+
+md_status md_get_thermostat(md_system *s, double *host_out) {
+  if (!s || !host_out) return MD_ERR_INVALID_ARG;
+  std::vector<double> nh(kNhFields * (size_t)s->a.R);
+  MD_CUDA(cudaDeviceSynchronize());
+  MD_CUDA(cudaMemcpy(nh.data(), s->a.nh, sizeof(double) * nh.size(), cudaMemcpyDeviceToHost));
+  for (int r = 0; r < s->a.R; r++) {  // the state between steps
+    host_out[2 * r] = nh[kNhFields * r + 4];
+    host_out[2 * r + 1] = nh[kNhFields * r + 5];
   }
   return MD_OK;
 }

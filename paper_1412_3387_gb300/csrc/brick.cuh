@@ -45,9 +45,14 @@
 // kernel's lanes per particle; one group is one warp's work).  Group j
 // (particles jP .. jP + Pj - 1, at cell-list positions hstart + jP ...) keeps
 // its rows in the list region reserved for those particles, starting at
-// (hstart + jP) * max_nb, as T_j tiles: entry k of the group's particle q sits
-// at ((k / W) * Pj + q) * W + k % W, T_j = ceil(max row length / W), so a
-// warp's W lanes per particle read consecutive entries.
+// (hstart + jP) * max_nb.  Entry k of the group's particle q belongs to tile
+// t = k / W and lane l = q W + k % W; V = row_depth(W) consecutive tiles of
+// one lane are contiguous:
+//   offset(k) = ((t / V) Pj W + l) V + t % V,
+// so a lane reads V entries (8 bytes for W <= 8) with one load and a warp
+// reads whole 32-byte sectors.  A group's tile count T_j (nl_tiles) is its
+// longest row's ceil(length / W) rounded up to a multiple of V; shorter rows
+// are padded with the sentinel entry.
 //
 // A brick whose stage does not fit the buffer (an unusually dense region) is
 // "direct": its positions are read from global memory instead.
@@ -58,6 +63,17 @@
 namespace mdgb {
 
 constexpr int kStageCells = 64;
+
+// Consecutive tiles of one lane stored together in the row layout.
+__host__ __device__ constexpr int row_depth(int W) { return W <= 8 ? 4 : 32 / W; }
+
+// Offset of entry k of the group's particle q from the group's base (row
+// layout above); lw = log2 W, pj = particles in the group.
+__device__ __forceinline__ int row_offset(int k, int lw, int pj, int q) {
+  const int lv = lw <= 3 ? 2 : 5 - lw;  // log2 row_depth(1 << lw)
+  const int t = k >> lw;
+  return ((((t >> lv) * pj + q) << lw) + (k & ((1 << lw) - 1))) * (1 << lv) + (t & ((1 << lv) - 1));
+}
 constexpr float kFar = 1e30f;  // sentinel coordinate
 constexpr int kMaxBrickThreads = 512;
 constexpr int kStagePad = 8;  // slots past a stage that the list build may read (not use)
@@ -169,6 +185,13 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// Asks the memory system to bring `bytes` (a multiple of 16; address 16-byte
+// aligned) of global memory into L2 ahead of use (a hint: no data moves to
+// the SM, nothing waits for it).
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 // Orders this thread's generic-proxy shared-memory accesses before later

@@ -59,10 +59,7 @@ __device__ __forceinline__ bool finite_bits(double x) {
   return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
 }
 
-__device__ __forceinline__ void kick_drift(double &x, double &v, int &img, double f, double hk,
-                                           double dt, double L) {
-  v = fma(hk, f, v);
-  x = fma(dt, v, x);
+__device__ __forceinline__ void wrap_coord(double &x, int &img, double L) {
   if (outside_box(x, __double_as_longlong(L)) && finite_bits(x)) {
     double k = floor(x / L);
     k = fmin(fmax(k, -1e9), 1e9);
@@ -71,6 +68,38 @@ __device__ __forceinline__ void kick_drift(double &x, double &v, int &img, doubl
     if (x >= L) { x = __dsub_rn(x, L); img++; }
     if (x < 0.0) { x = __dadd_rn(x, L); img--; }
   }
+}
+
+__device__ __forceinline__ void kick_drift(double &x, double &v, int &img, double f, double hk,
+                                           double dt, double L) {
+  v = fma(hk, f, v);
+  x = fma(dt, v, x);
+  wrap_coord(x, img, L);
+}
+
+// Langevin BAOAB, first part, one coordinate: kick (B), half drift (A),
+// Ornstein-Uhlenbeck step v = c v + sig theta (O), half drift (A), wrap.
+__device__ __forceinline__ void baoab_coord(double &x, double &v, int &img, double f, double hk,
+                                            double hdt, double c, double sig, double theta,
+                                            double L) {
+  v = fma(hk, f, v);
+  x = fma(hdt, v, x);
+  v = fma(c, v, sig * theta);
+  x = fma(hdt, v, x);
+  wrap_coord(x, img, L);
+}
+
+// Langevin noise of one particle for time step `step`: theta_k = sqrt(3)
+// (2 u_k - 1), u_k = (w_k + 1/2) 2^-32, words 0..2 of Philox-4x32-10 with
+// counter (tag, 0xFFFFFFFF, step lo, step hi) and key (seed lo, seed hi).
+// Every operation after the integer generator is exact in FP64.
+__device__ __forceinline__ void langevin_theta(int32_t tag, uint64_t step, uint64_t seed,
+                                               double th[3]) {
+  const U4 c{(uint32_t)tag, 0xFFFFFFFFu, (uint32_t)step, (uint32_t)(step >> 32)};
+  const U4 w = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  th[0] = 1.7320508075688772 * (2.0 * (((double)w.x + 0.5) * 2.3283064365386963e-10) - 1.0);
+  th[1] = 1.7320508075688772 * (2.0 * (((double)w.y + 0.5) * 2.3283064365386963e-10) - 1.0);
+  th[2] = 1.7320508075688772 * (2.0 * (((double)w.z + 0.5) * 2.3283064365386963e-10) - 1.0);
 }
 
 // Velocity Verlet, first half, fused with the frame refresh of the FP32
@@ -93,9 +122,26 @@ __global__ void k_integrate1(KArgs a, double hk) {
     const double3 f = ld_force3(a, i);
     int4 img = a.image[i];
     const int4 img0 = img;
-    kick_drift(x.x, v.x, img.x, f.x, hk, a.dt, rp.L[0]);
-    kick_drift(x.y, v.y, img.y, f.y, hk, a.dt, rp.L[1]);
-    kick_drift(x.z, v.z, img.z, f.z, hk, a.dt, rp.L[2]);
+    if (a.integ == MD_NOSE_HOOVER) {
+      // the thermostat's half steps at the end of the previous step and at
+      // the start of this one, in that order
+      const double s1 = a.nh[kNhFields * r + 3], s2 = a.nh[kNhFields * r + 2];
+      v.x = (v.x * s1) * s2;
+      v.y = (v.y * s1) * s2;
+      v.z = (v.z * s1) * s2;
+    }
+    if (a.integ == MD_LANGEVIN) {
+      double th[3];
+      langevin_theta(a.tag[i], (uint64_t)(t + 1), a.t_seed, th);
+      const double hdt = 0.5 * a.dt;
+      baoab_coord(x.x, v.x, img.x, f.x, hk, hdt, a.t_c, a.t_sig, th[0], rp.L[0]);
+      baoab_coord(x.y, v.y, img.y, f.y, hk, hdt, a.t_c, a.t_sig, th[1], rp.L[1]);
+      baoab_coord(x.z, v.z, img.z, f.z, hk, hdt, a.t_c, a.t_sig, th[2], rp.L[2]);
+    } else {
+      kick_drift(x.x, v.x, img.x, f.x, hk, a.dt, rp.L[0]);
+      kick_drift(x.y, v.y, img.y, f.y, hk, a.dt, rp.L[1]);
+      kick_drift(x.z, v.z, img.z, f.z, hk, a.dt, rp.L[2]);
+    }
     st_d4(a.pos + i, x);
     st_d4(a.vel + i, v);
     if (img.x != img0.x || img.y != img0.y || img.z != img0.z) a.image[i] = img;
@@ -159,6 +205,110 @@ __global__ void k_integrate2(KArgs a) {
   v.y = fma(hk, f.y, v.y);
   v.z = fma(hk, f.z, v.z);
   st_d4(a.vel + i, v);
+}
+
+// One Nose-Hoover half step (the factor exp(iL_T dt/2) of the Trotter
+// splitting) from the kinetic energy KE of a replica's g = 3N - 3 degrees of
+// freedom; returns the velocity scale and updates KE, xi, eta.
+__device__ __forceinline__ double nh_half(const KArgs &a, double g, double &KE, double &xi,
+                                          double &eta) {
+  xi += 0.25 * a.dt * ((2.0 * KE / g) / a.t_kT - 1.0) / (a.t_tau * a.t_tau);
+  const double sc = exp(-0.5 * a.dt * xi);
+  eta += 0.5 * a.dt * xi;
+  KE *= sc * sc;
+  xi += 0.25 * a.dt * ((2.0 * KE / g) / a.t_kT - 1.0) / (a.t_tau * a.t_tau);
+  return sc;
+}
+
+// Nose-Hoover: second half-kick (kick = 1) or none (kick = 0: the start of a
+// sequence of steps) and the kinetic-energy sum, one block per thermo chunk
+// (fixed assignment and tree: bitwise reproducible).  The last block takes,
+// per replica, the thermostat's half step at the end of this step (its scale
+// s1 stays pending: the velocities in memory are the unscaled ones) and the
+// one at the start of the next step (s2); the next first half applies both.
+__global__ void __launch_bounds__(256) k_nh_kick_sum(KArgs a, int kick) {
+  __shared__ double sh[256];
+  __shared__ int is_last;
+  const int64_t ch = blockIdx.x;
+  const int r = a.tchunk_rep[ch];
+  const Rep &rp = a.rep[r];
+  const int64_t p0 = rp.p0 + (ch - rp.tchunk0) * kThermoChunk;
+  const int64_t p1 = min(p0 + kThermoChunk, rp.p1);
+  const double hk = a.half_dt_m;
+  double ke = 0.0;
+  for (int64_t i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+    double4 v = ld_d4_plain(a.vel + i);
+    if (kick) {
+      const double3 f = ld_force3(a, i);
+      v.x = fma(hk, f.x, v.x);
+      v.y = fma(hk, f.y, v.y);
+      v.z = fma(hk, f.z, v.z);
+      st_d4(a.vel + i, v);
+    }
+    ke += 0.5 * a.mass * (v.x * v.x + v.y * v.y + v.z * v.z);
+  }
+  sh[threadIdx.x] = ke;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.nh_part[ch] = sh[0];
+    __threadfence();
+    is_last = atomicAdd(&a.ds->nh_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int q = threadIdx.x; q < a.R; q += blockDim.x) {
+    const Rep &rq = a.rep[q];
+    const double g = 3.0 * (double)(rq.p1 - rq.p0) - 3.0;
+    if (!(g > 0.0)) continue;
+    double KE = 0.0;
+    for (int c = 0; c < rq.ntchunk; c++) KE += __ldcg(a.nh_part + rq.tchunk0 + c);
+    double *st = a.nh + kNhFields * q;
+    double xi = st[0], eta = st[1];
+    const double s1 = kick ? nh_half(a, g, KE, xi, eta) : st[3];
+    // the state between steps (after this step's end half step) is the one
+    // reported; the next step starts from its start half step
+    st[4] = xi;
+    st[5] = eta;
+    const double s2 = nh_half(a, g, KE, xi, eta);
+    st[0] = xi;
+    st[1] = eta;
+    st[2] = s2;
+    st[3] = s1;
+  }
+  if (threadIdx.x == 0) a.ds->nh_done = 0u;
+}
+
+// Applies the pending end-of-step scale s1 to the velocities (the state after
+// a completed step); k_nh_flush_end then clears it.
+__global__ void k_nh_flush(KArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const double s1 = a.nh[kNhFields * replica_of(a, i) + 3];
+  double4 v = ld_d4_plain(a.vel + i);
+  v.x *= s1;
+  v.y *= s1;
+  v.z *= s1;
+  st_d4(a.vel + i, v);
+}
+
+__global__ void k_nh_flush_end(KArgs a) {
+  for (int q = threadIdx.x; q < a.R; q += blockDim.x) {
+    // the start-of-next-step scale was computed from the scaled energy
+    a.nh[kNhFields * q + 3] = 1.0;
+  }
+}
+
+__global__ void k_nh_reset(KArgs a) {
+  for (int q = threadIdx.x; q < a.R; q += blockDim.x) {
+    double *st = a.nh + kNhFields * q;
+    st[0] = st[1] = st[4] = st[5] = 0.0;
+    st[2] = st[3] = 1.0;
+  }
 }
 
 // Harmonic bonds (Sec. 4.3.4: a bond is an unordered pair of particle IDs):
@@ -277,6 +427,14 @@ __global__ void k_thermo_final(KArgs a, double *out, int from_run) {
     if (row < 0 || row >= ds->thermo_rows) return;
     o = ds->thermo_out + row * (int64_t)a.R * 8;
   }
+  if (a.integ == MD_NOSE_HOOVER) {
+    // the velocities lack the thermostat's pending end-of-step scale
+    const double sc = a.nh[kNhFields * r + 3];
+    s[0] *= sc * sc;
+    s[3] *= sc;
+    s[4] *= sc;
+    s[5] *= sc;
+  }
   const double n = (double)(rp.p1 - rp.p0);
   double *q = o + 8 * r;
   q[0] = s[0];
@@ -361,7 +519,7 @@ __global__ void k_export_nlist(KArgs a, int32_t *counts, int32_t *rows) {
     for (int k0 = 0; k0 < T * W; k0 += 32) {
       const int k = k0 + lane;
       int e = 0;
-      if (k < T * W) e = grp[((k >> lw) * pj + q2) * W + (k & (W - 1))];
+      if (k < T * W) e = grp[row_offset(k, lw, pj, q2)];
       const unsigned m = __ballot_sync(0xffffffffu, e > 0);
       if (e > 0) {
         const int at = n + __popc(m & ((1u << lane) - 1u));
@@ -402,7 +560,27 @@ cudaError_t launch_integrate1(const KArgs &a, cudaStream_t st, bool fold_kick) {
 
 cudaError_t launch_integrate2(const KArgs &a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  k_integrate2<<<blocks_for(a.n, 256), 256, 0, st>>>(a);
+  if (a.integ == MD_NOSE_HOOVER) {
+    if (a.n_tchunks > 0) k_nh_kick_sum<<<(unsigned)a.n_tchunks, 256, 0, st>>>(a, 1);
+  } else {
+    k_integrate2<<<blocks_for(a.n, 256), 256, 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nh_begin(const KArgs &a, cudaStream_t st) {
+  if (a.n_tchunks > 0) k_nh_kick_sum<<<(unsigned)a.n_tchunks, 256, 0, st>>>(a, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nh_flush(const KArgs &a, cudaStream_t st) {
+  if (a.n > 0) k_nh_flush<<<blocks_for(a.n, 256), 256, 0, st>>>(a);
+  k_nh_flush_end<<<1, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nh_reset(const KArgs &a, cudaStream_t st) {
+  k_nh_reset<<<1, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 

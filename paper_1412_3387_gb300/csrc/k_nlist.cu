@@ -51,22 +51,23 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
   const StageSrc<DIRECT> src{a, d, rp, smem_u32(spos), 0u};
   const float4 oi = src.pos((uint32_t)(hs.slot + 1));
   const float lo2 = a.rl2f - rp.band, hi2 = a.rl2f + rp.band;
-  // a block with some |r^2 - r_list^2| within the band (a little room for the
-  // rounding of the band's ends) goes through the FP64 re-test
-  const float bthr = 1.001f * rp.band;
+  // a block with some r^2 in the band [lo2, hi2) goes through the FP64
+  // re-test: bthr is the larger exact distance of the rounded band ends from
+  // r_list^2, so |r^2 - r_list^2| <= bthr for every r^2 in the band
+  const float bthr = fmaxf(a.rl2f - lo2, hi2 - a.rl2f);
   const uint64_t oixy = pack2(oi.x, oi.y);
   const int max_nb = a.max_nb;
   // the pair kernel's row layout: groups of Pp = 32 / Wp particles, tiles of
   // Wp entries per particle; the row's entry k sits in tile k / Wp, column k % Wp
   const int lwp = a.w_store_log2, Wp = 1 << lwp, Pp = 32 >> lwp;
-  const int tcap = max_nb >> lwp;  // tiles a row region holds
+  const int Vp = row_depth(Wp);
+  const int tcap = max_nb >> lwp;  // tiles a row region holds (a multiple of Vp)
   const int gq = j * PB + qe;      // the particle's place in the brick
   const int grp = gq / Pp, q2 = gq - grp * Pp;
   const int pj = min(Pp, d.nhome - grp * Pp);
   uint16_t *gbase = a.nl + (size_t)(d.hstart + grp * Pp) * (size_t)max_nb;
   auto put = [&](int k, uint16_t v) {
-    const int t = k >> lwp;
-    if (t < tcap) gbase[((t * pj + q2) << lwp) + (k & (Wp - 1))] = v;
+    if ((k >> lwp) < tcap) gbase[row_offset(k, lwp, pj, q2)] = v;
   };
   // the nine runs of the particle's 3 x 3 x 3 stencil: stage cells
   // (hx .. hx + 2, hy + dy, hz + dz) for the home cell (hx + 1, hy + 1, hz + 1)
@@ -210,7 +211,7 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
   int tg = tq;
   const int glanes = Pp * WB;
   for (int o = 1; o < glanes; o <<= 1) tg = max(tg, __shfl_xor_sync(FULL, tg, o));
-  tg = min(tg, tcap);
+  tg = min((tg + Vp - 1) / Vp * Vp, tcap);  // whole blocks of Vp tiles
   if (active && sl == 0) {
     a.n_nb[p] = n;
     if (tq > tcap) {

@@ -14,6 +14,7 @@ namespace mdgb {
 constexpr int kMaxTypes = 32;
 constexpr int kChunkCells = 2048;     // cells per scan chunk (256 threads x 8)
 constexpr int kThermoChunk = 4096;    // particles per thermo partial sum
+constexpr int kNhFields = 6;          // Nose-Hoover state doubles per replica
 constexpr int kMaxCellSort = 256;     // largest cell the in-cell sort handles
 constexpr int kCellBits = 9;          // packed cell coordinate bits (nc <= 512)
 // Largest system: 2^27 particles (about 80 GB of state and list at the
@@ -79,6 +80,7 @@ struct DevState {
   int32_t rebuild_any;   // some replica's rebuild flag is raised for the current step
   int64_t n_builds;      // replica list builds so far
   int64_t thermo_rows;   // md_run: capacity of thermo_out in rows
+  uint32_t nh_done;      // Nose-Hoover reduction last-block ticket
 };
 
 // Pair coefficients, prepared on the host.
@@ -153,6 +155,13 @@ struct KArgs {
   double dt, mass, kT;
   double half_dt_m;    // dt / (2 m), computed once on the host
   double bond_K, bond_r0;
+  // thermostat (md_set_integrator)
+  int32_t integ;         // md_integrator
+  double t_kT, t_c, t_sig, t_tau;  // kT; Langevin exp(-gamma dt), sqrt((1 - c^2) kT / m); NH tau
+  uint64_t t_seed;
+  double *nh;            // [R][kNhFields] Nose-Hoover: xi, eta (for the next step), start-of-step
+                         // scale, pending end-of-step scale, xi, eta between steps (reported)
+  double *nh_part;       // [thermo chunks] kinetic-energy partial sums
   float disp2_f;       // (r_skin / 2)^2, slightly reduced
   uint64_t seed;
   int64_t n_chunks, n_tchunks, n_cells, n_bricks;
@@ -261,6 +270,12 @@ struct Launch { int block; int w; };
 // fold_kick: also apply the previous step's second half-kick (it was left out)
 cudaError_t launch_integrate1(const KArgs &a, cudaStream_t st, bool fold_kick = false);
 cudaError_t launch_integrate2(const KArgs &a, cudaStream_t st);
+// Nose-Hoover: sum the kinetic energy and take the thermostat's half step
+// (begin = 1: at the start of a sequence of steps, without a kick); flush:
+// apply the pending end-of-step scale to the velocities.
+cudaError_t launch_nh_begin(const KArgs &a, cudaStream_t st);
+cudaError_t launch_nh_flush(const KArgs &a, cudaStream_t st);
+cudaError_t launch_nh_reset(const KArgs &a, cudaStream_t st);
 cudaError_t launch_bin(const KArgs &a, int force, cudaStream_t st);
 cudaError_t launch_sort(const KArgs &a, int force, cudaStream_t st);
 cudaError_t launch_nlist(const KArgs &a, Launch l, int force, cudaStream_t st);

@@ -150,9 +150,14 @@ __global__ void k_na_forces(const double4 *pos, int64_t n, Grid g, double rc2, d
       int32_t j = members[k];
       if (j == i) continue;
       double4 xj = pos[j];
-      double d[3] = {xi.x - xj.x, xi.y - xj.y, xi.z - xj.z};
-      for (int a = 0; a < 3; a++) d[a] -= g.L[a] * rint(d[a] * g.inv_L[a]);
-      double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      // minimum image and r^2 rounded step by step (no fused multiply-add),
+      // as in the regular path's exact distance: with a fused L rint(d / L)
+      // a separation across the boundary would move by up to an ulp of L
+      double d[3] = {__dsub_rn(xi.x, xj.x), __dsub_rn(xi.y, xj.y), __dsub_rn(xi.z, xj.z)};
+      for (int a = 0; a < 3; a++)
+        d[a] = __dsub_rn(d[a], __dmul_rn(g.L[a], rint(__dmul_rn(d[a], g.inv_L[a]))));
+      double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])),
+                            __dmul_rn(d[2], d[2]));
       if (r2 >= rc2) continue;
       double r2i = 1.0 / r2, r6 = r2i * r2i * r2i;
       double fr = r2i * r6 * (lj1 * r6 - lj2);

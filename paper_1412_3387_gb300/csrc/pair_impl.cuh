@@ -184,20 +184,58 @@ struct DoublePair {
   }
 };
 
+// V consecutive 16-bit row entries of one lane, loaded with one instruction.
+template <int V> struct RowWord;
+template <> struct RowWord<4> {
+  using T = uint2;
+  static __device__ __forceinline__ T load(const uint16_t *p) {
+    return __ldcs(reinterpret_cast<const uint2 *>(p));
+  }
+  static __device__ __forceinline__ T zero() { return make_uint2(0u, 0u); }
+  static __device__ __forceinline__ uint32_t get(const T &w, int v) {
+    const uint32_t x = v < 2 ? w.x : w.y;
+    return (v & 1) ? x >> 16 : x & 0xffffu;
+  }
+};
+template <> struct RowWord<2> {
+  using T = uint32_t;
+  static __device__ __forceinline__ T load(const uint16_t *p) {
+    return __ldcs(reinterpret_cast<const unsigned int *>(p));
+  }
+  static __device__ __forceinline__ T zero() { return 0u; }
+  static __device__ __forceinline__ uint32_t get(const T &w, int v) {
+    return (v & 1) ? w >> 16 : w & 0xffffu;
+  }
+};
+template <> struct RowWord<1> {
+  using T = uint32_t;
+  static __device__ __forceinline__ T load(const uint16_t *p) {
+    return (uint32_t)__ldcs(reinterpret_cast<const unsigned short *>(p));
+  }
+  static __device__ __forceinline__ T zero() { return 0u; }
+  static __device__ __forceinline__ uint32_t get(const T &w, int) { return w; }
+};
+
 // One row group (P = 32 / W particles of the brick, W lanes each) on one
-// warp.  Rows are read from global memory one block of U tiles ahead.  FULLG:
-// the group has all P particles, so a tile is 32 entries and every row offset
-// is a compile-time constant.
+// warp.  Each lane walks its particle's row in blocks of V entries (one load
+// per block, two blocks loaded ahead); a group's rows are padded to whole
+// blocks, so every block is processed by the same code.  The mixed forms are
+// branch-free: every entry is evaluated (the sentinel's r^2 is +inf) and
+// masked by r^2 < r_cut^2; entries whose FP32 r^2 lies in the error band
+// around r_cut^2 are settled in FP64 after each pair of blocks.  FULLG: the
+// group has all P particles (a block is 32 V entries).
 template <int POT, int W, bool MIXED, bool ENERGY, bool ONE, bool DIRECT, bool FULLG>
 __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, const float4 *spos,
                                            const float4 *svel, int j, uint64_t step) {
   constexpr int P = 32 / W;
-  constexpr int U = 8;
+  constexpr int V = row_depth(W);
+  using RW = RowWord<V>;
+  using Word = typename RW::T;
   const int lane = threadIdx.x & 31;
   const int qq = lane / W, sl = lane & (W - 1);
   const int q = j * P + qq;
   const bool active = q < d.nhome;
-  const int pj = min(P, d.nhome - j * P);
+  const int pj = FULLG ? P : min(P, d.nhome - j * P);
   const int qe = active ? qq : 0;  // idle lanes shadow the group's first particle
   const Rep &rp = a.rep[d.r];
   const bool ident = a.ident[d.r] != 0;
@@ -207,9 +245,10 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
   const StageSrc<DIRECT> src{a, d, rp, smem_u32(spos), smem_u32(svel)};
   const float4 oi = src.pos((uint32_t)(hs.slot + 1));
   const int pg = d.hstart + j * P;
-  const int T = __ldg(a.nl_tiles + pg);
-  const uint16_t *rows = a.nl + (size_t)pg * (size_t)a.max_nb + qe * W + sl;
-  const int stride = FULLG ? 32 : pj * W;  // entries per tile
+  const int NB = __ldg(a.nl_tiles + pg) / V;        // blocks of V tiles
+  const int bstride = (FULLG ? 32 : pj * W) * V;    // entries per block
+  const uint16_t *row = a.nl + (size_t)pg * (size_t)a.max_nb + (qe * W + sl) * V;
+  auto ldrow = [&](int b) { return b < NB ? RW::load(row + (size_t)b * bstride) : RW::zero(); };
 
   KSum kf[3], kpe, kw[6];
   double df[3] = {0., 0., 0.}, dpe = 0., dw[6] = {0., 0., 0., 0., 0., 0.};
@@ -249,107 +288,135 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
     }
   }
 
-  // the mixed LJ block test: an entry with |r^2 - r_cut^2| within the band
-  // (with a little room for the rounding of the band's ends) sends the block
-  // through the FP64 re-test
+  // an entry with r^2 in the band [lo, hi) sends its pair of blocks through
+  // the FP64 re-test.  The band's ends are rounded FP32 numbers; bthr is the
+  // larger of their exact distances from r_cut^2 (differences of nearby FP32
+  // numbers are exact), and |r^2 - r_cut^2| <= bthr holds for every r^2 in
+  // [lo, hi), so no band entry escapes the re-test.
   const uint64_t oixy = pack2(oi.x, oi.y);
-  const float rc2f = a.rc2f, bthr = 1.001f * rp.band;
+  const float rc2f = a.rc2f;
+  const float lo = mp.rc2_lo;
+  const float bthr = fmaxf(rc2f - lo, mp.rc2_hi - rc2f);
 
-  // U entries at a time; the full blocks load the next block ahead without
-  // bounds tests, the last T mod U tiles go one at a time (nu = 1)
-  auto work = [&](const uint32_t *e, const int nu) {
-    float gx = 0.f, gy = 0.f, gz = 0.f;
-    if (MIXED && POT == kLJ) {
-      // straight-line LJ: every entry is evaluated and masked (the sentinel's
-      // r^2 is +inf); entries in the FP64 tie-break band are settled after
-      // the group
-      float bmin = 3.0e38f;  // smallest |r^2 - r_cut^2| of the block
+  // FP32 separation of the home particle from the neighbour of entry e
+  auto sep = [&](uint32_t e, float &dx, float &dy, float &dz, float &ojw) {
+    if (DIRECT) {
+      const float4 oj = src.pos(e);
+      dx = oi.x - oj.x;
+      dy = oi.y - oj.y;
+      dz = oi.z - oj.z;
+      ojw = oj.w;
+    } else {
+      const float4 oj = spos[e];
+      const float2 dxy = unpack2(sub_f32x2(oixy, pack2(oj.x, oj.y)));
+      dx = dxy.x;
+      dy = dxy.y;
+      dz = oi.z - oj.z;
+      ojw = oj.w;
+    }
+  };
+
+  // the V entries of one block, mixed precision: group sums (gx, gy, gz),
+  // smallest |r^2 - r_cut^2| in bmin
+  auto mixed_block = [&](const Word &w, float &gx, float &gy, float &gz, float &bmin) {
 #pragma unroll
-      for (int u = 0; u < nu; u++) {
-        float dx, dy, dz, ojw;
-        if (DIRECT) {
-          const float4 oj = src.pos(e[u]);
-          dx = oi.x - oj.x;
-          dy = oi.y - oj.y;
-          dz = oi.z - oj.z;
-          ojw = oj.w;
-        } else {
-          uint64_t xy, zw;
-          lds_pairs(src.spos + e[u] * 16u, xy, zw);
-          const float2 dxy = unpack2(sub_f32x2(oixy, xy));
-          const float2 ozw = unpack2(zw);
-          dx = dxy.x;
-          dy = dxy.y;
-          dz = oi.z - ozw.x;
-          ojw = ozw.y;
-        }
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const bool in = r2 < mp.rc2_lo;
-        bmin = fminf(bmin, fabsf(r2 - rc2f));
+    for (int v = 0; v < V; v++) {
+      const uint32_t e = RW::get(w, v);
+      float dx, dy, dz, ojw;
+      sep(e, dx, dy, dz, ojw);
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      const bool in = r2 < lo;
+      bmin = fminf(bmin, fabsf(r2 - rc2f));
+      float fr, en = 0.f;
+      if (POT == kLJ) {
         const LJCoeffF c = ONE ? mp.lj0
                                : reinterpret_cast<const LJCoeffF *>(a.coeff)[
                                      mp.ti * a.ntypes + cell_type(__float_as_uint(ojw))];
         const float r2i = __fdividef(1.0f, r2);
         const float r6 = r2i * r2i * r2i;
-        const float fr = in ? r2i * r6 * (c.lj1 * r6 - c.lj2) : 0.f;
-        gx = fmaf(fr, dx, gx);
-        gy = fmaf(fr, dy, gy);
-        gz = fmaf(fr, dz, gz);
-        if (ENERGY) {
-          const float v = in ? r6 * (c.lj3 * r6 - c.lj4) - c.vshift : 0.f;
-          const float fx = fr * dx, fy = fr * dy, fz = fr * dz;
-          kpe.add(0.5f * v);
-          kw[0].add(0.5f * dx * fx); kw[1].add(0.5f * dx * fy); kw[2].add(0.5f * dx * fz);
-          kw[3].add(0.5f * dy * fy); kw[4].add(0.5f * dy * fz); kw[5].add(0.5f * dz * fz);
-        }
+        fr = in ? r2i * r6 * (c.lj1 * r6 - c.lj2) : 0.f;
+        if (ENERGY) en = in ? r6 * (c.lj3 * r6 - c.lj4) - c.vshift : 0.f;
+      } else {
+        const DPDCoeffF c = ONE ? mp.dp0
+                                : reinterpret_cast<const DPDCoeffF *>(a.coeff)[
+                                      mp.ti * a.ntypes + cell_type(__float_as_uint(ojw))];
+        const float4 vj = DIRECT ? src.vel(e) : reinterpret_cast<const float4 *>(svel)[e];
+        const float rinv = rsqrtf(r2);
+        const float wgt = fmaf(-r2 * rinv, mp.inv_rc, 1.f);
+        const float dot = dx * (mp.vi4.x - vj.x) + dy * (mp.vi4.y - vj.y) + dz * (mp.vi4.z - vj.z);
+        const uint32_t word = dpd_word(mp.tag_i, __float_as_int(vj.w), step, a.seed);
+        const float uu = ((float)(word >> 8) + 0.5f) * 5.9604644775390625e-08f;  // 2^-24
+        const float theta = 1.7320508075688772f * (2.f * uu - 1.f);
+        const float fmag = c.A * wgt - c.gamma * wgt * wgt * dot * rinv + c.sigma_rdt * wgt * theta;
+        fr = in ? fmag * rinv : 0.f;
+        if (ENERGY) en = in ? 0.5f * c.A * (float)a.r_cut * wgt * wgt : 0.f;
       }
-      if (__any_sync(FULL, bmin <= bthr)) {
-#pragma unroll
-        for (int u = 0; u < nu; u++) {
-          const float4 oj = src.pos(e[u]);
-          const float dx = oi.x - oj.x, dy = oi.y - oj.y, dz = oi.z - oj.z;
-          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          if (r2 >= mp.rc2_lo && r2 < mp.rc2_hi) mp(e[u], gx, gy, gz, kpe, kw);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int u = 0; u < nu; u++) {
-        if (e[u] == 0u) continue;  // padding
-        if (MIXED) mp(e[u], gx, gy, gz, kpe, kw);
-        else dp(e[u], df, dpe, dw);
+      gx = fmaf(fr, dx, gx);
+      gy = fmaf(fr, dy, gy);
+      gz = fmaf(fr, dz, gz);
+      if (ENERGY) {
+        const float fx = fr * dx, fy = fr * dy, fz = fr * dz;
+        kpe.add(0.5f * en);
+        kw[0].add(0.5f * dx * fx); kw[1].add(0.5f * dx * fy); kw[2].add(0.5f * dx * fz);
+        kw[3].add(0.5f * dy * fy); kw[4].add(0.5f * dy * fz); kw[5].add(0.5f * dz * fz);
       }
     }
+  };
+  // the block's entries inside the FP32 band: decided in FP64 (rare)
+  auto band_block = [&](const Word &w, float &gx, float &gy, float &gz) {
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      const uint32_t e = RW::get(w, v);
+      float dx, dy, dz, ojw;
+      sep(e, dx, dy, dz, ojw);
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      if (r2 >= mp.rc2_lo && r2 < mp.rc2_hi) mp(e, gx, gy, gz, kpe, kw);
+    }
+  };
+  auto fp64_block = [&](const Word &w) {
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      const uint32_t e = RW::get(w, v);
+      if (e != 0u) dp(e, df, dpe, dw);  // 0: padding
+    }
+  };
+
+  // two blocks (a Kahan flush and at most one FP64 band pass) per step
+  auto two_blocks = [&](const Word &w0, const Word &w1, bool two) {
     if (MIXED) {
+      float gx = 0.f, gy = 0.f, gz = 0.f, bmin = 3.0e38f;
+      mixed_block(w0, gx, gy, gz, bmin);
+      if (two) mixed_block(w1, gx, gy, gz, bmin);
+      if (__any_sync(FULL, bmin <= bthr)) {
+        band_block(w0, gx, gy, gz);
+        if (two) band_block(w1, gx, gy, gz);
+      }
       kf[0].add(gx);
       kf[1].add(gy);
       kf[2].add(gz);
+    } else {
+      fp64_block(w0);
+      if (two) fp64_block(w1);
     }
   };
-  const int Tm = T & ~(U - 1);
-  uint32_t nxt[U];
-#pragma unroll
-  for (int u = 0; u < U; u++) nxt[u] = u < T ? (uint32_t)__ldcs(rows + u * stride) : 0u;
-  for (int t0 = 0; t0 < Tm; t0 += U) {
-    uint32_t e[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) e[u] = nxt[u];
-    const uint16_t *r = rows + (size_t)(t0 + U) * stride;
-    if (t0 + 2 * U <= T) {
-#pragma unroll
-      for (int u = 0; u < U; u++) nxt[u] = (uint32_t)__ldcs(r + u * stride);
-    } else {
-      // the tail tiles come in with the last full block
-#pragma unroll
-      for (int u = 0; u < U; u++) nxt[u] = t0 + U + u < T ? (uint32_t)__ldcs(r + u * stride) : 0u;
+  // four blocks in flight per lane: the row stream is latency-bound, so the
+  // bytes a warp keeps in flight set its speed (the next brick's rows are
+  // also being prefetched into L2)
+  Word q0 = ldrow(0), q1 = ldrow(1), q2 = ldrow(2), q3 = ldrow(3);
+  for (int b = 0; b < NB; b += 4) {  // NB is warp-uniform: so are all branches here
+    {
+      const Word w0 = q0, w1 = q1;
+      q0 = ldrow(b + 4);
+      q1 = ldrow(b + 5);
+      two_blocks(w0, w1, b + 1 < NB);
     }
-    work(e, U);
+    if (b + 2 < NB) {
+      const Word w0 = q2, w1 = q3;
+      q2 = ldrow(b + 6);
+      q3 = ldrow(b + 7);
+      two_blocks(w0, w1, b + 3 < NB);
+    }
   }
-  // the last T mod U tiles, already loaded, one at a time
-  const int rem = T - Tm;
-#pragma unroll
-  for (int u = 0; u < U; u++)
-    if (u < rem) work(&nxt[u], 1);
 
   // combine the W partial sums of each particle (intra-warp reduction)
   if (MIXED) {
@@ -438,8 +505,16 @@ __global__ void __launch_bounds__(kMaxBrickThreads) k_pair(KArgs a, int cap) {
     const long long bt = b0 + t * G;
     if (bt >= a.n_bricks) break;
     const bool has1 = bt + G < a.n_bricks, has2 = bt + 2 * G < a.n_bricks;
-    if (has1)
+    if (has1) {
       stage_issue(a, M.desc(t + 1), M.pos(t + 1), VEL ? M.vel4(t + 1) : nullptr, M.bar(t + 1), cap);
+      // the next brick's row region (its particles' reserved rows, a
+      // multiple of 64 bytes) into L2 while this brick is computed
+      if (threadIdx.x == (blockDim.x > 32 ? 32 : 0)) {
+        const BrickDesc &dn = M.desc(t + 1);
+        prefetch_l2(a.nl + (size_t)dn.hstart * (size_t)a.max_nb,
+                    (uint32_t)((size_t)dn.nhome * (size_t)a.max_nb * sizeof(uint16_t)));
+      }
+    }
     // the descriptor two bricks ahead: loaded now, stored after the work
     // (40 words; a block has at least 32 threads, so two per thread)
     uint4 dv0 = make_uint4(0u, 0u, 0u, 0u), dv1 = dv0;

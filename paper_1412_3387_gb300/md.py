@@ -75,7 +75,10 @@ SIGNATURES = {
     "md_get_info": (C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I64)]),
     "md_philox4x32_10": (C.c_int, [_P, _P, _I64, _P]),
     "md_lj_forces_noalloc": (C.c_int, [_P, _I64, _P, _D, _D, _D, _P, _P]),
+    "md_set_integrator": (C.c_int, [_P, _I32, _D, _D, C.c_uint64]),
+    "md_get_thermostat": (C.c_int, [_P, _P]),
 }
+INTEGRATORS = {"nve": 0, "langevin": 1, "nose-hoover": 2}
 
 _lib = None
 
@@ -257,6 +260,19 @@ class MDSystem:
         out = torch.zeros((self.R, 8), dtype=torch.float64, device=self.device)
         check(self.lib.md_reduce_thermo(self.handle, _ptr(out), _stream(stream)),
               "md_reduce_thermo")
+        return out
+
+    def set_integrator(self, kind="nve", kT=1.0, param=1.0, seed=0):
+        """kind: "nve", "langevin" (param = friction gamma) or "nose-hoover"
+        (param = thermostat period tau); see md_set_integrator."""
+        check(self.lib.md_set_integrator(self.handle, INTEGRATORS[kind], float(kT), float(param),
+                                         int(seed)), "md_set_integrator")
+
+    def thermostat(self):
+        """Nose-Hoover (xi, eta) per replica, float64 numpy [R, 2]."""
+        out = np.zeros((self.R, 2))
+        check(self.lib.md_get_thermostat(self.handle, out.ctypes.data_as(C.c_void_p)),
+              "md_get_thermostat")
         return out
 
     def autotune(self, n_samples=5, block_stride=1, stream=None):

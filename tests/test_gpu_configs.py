@@ -291,3 +291,95 @@ def test_dpd_thermostat_and_momentum_over_steps(prec):
         f_rms = math.sqrt(float(np.mean(np.sum(f * f, axis=1))))
         bound = 20 * 0.02 * math.sqrt(600) * U32 * math.sqrt(n_pairs) * f_rms
         assert p < bound, (p, bound)
+
+
+def library_band(L, r_cut, r_skin):
+    """The library's FP32 r^2 uncertainty band for a cubic box (the plan's
+    formula, restated here only to aim test pairs at the band's ends)."""
+    rl = r_cut + r_skin
+    nc = math.floor(L / (rl * (1 + 1e-12)))
+    h = L / nc
+    g = 2.0 ** -40
+    while True:
+        hq = 2 * g * round(h / (2 * g))
+        wq = g * round((L - nc * hq) / g)
+        omax = 0.5 * h + 0.5 * r_skin + nc * abs(hq - h) + g
+        if omax < g * 2 ** 22 and omax + 1.5 * hq + abs(wq) < g * 2 ** 24:
+            break
+        g *= 2
+    err = 2 * rl * math.sqrt(3) * 1.5 * g + 3 * 2.0 ** -24 * rl * rl
+    return max(64 * 2.0 ** -24 * (h + r_skin) ** 2, 4 * err)
+
+
+def band_ends_state(seed, L=60.0, r_cut=2.5, r_skin=0.3, n_per=100, spread=1.2e-5):
+    """Isolated pairs (every other particle farther than r_list + 0.5) whose
+    squared separation lies near an end of the FP32 band around r_cut^2 and
+    r_list^2: end + U(-spread, spread), with end = the FP32-rounded
+    target -+ band.  Their FP32 r^2 scatters across the ends by the grid
+    rounding of the offsets, so every way of landing near an end occurs."""
+    rng = np.random.default_rng(seed)
+    f32 = np.float32
+    band = f32(library_band(L, r_cut, r_skin))
+    ends = []
+    for target in (r_cut * r_cut, (r_cut + r_skin) ** 2):
+        t = f32(target)
+        ends += [float(f32(t - band)), float(f32(t + band))]
+    d_min = r_cut + r_skin + 0.5
+    pts = []
+
+    def free(x):
+        if not pts:
+            return True
+        d = np.array(pts) - x
+        d -= L * np.rint(d / L)
+        return np.min(np.einsum("ij,ij->i", d, d)) > d_min * d_min
+
+    for end in ends:
+        made = 0
+        while made < n_per:
+            a = rng.uniform(0.0, L, 3)
+            u = rng.standard_normal(3)
+            u /= np.linalg.norm(u)
+            r = math.sqrt(end + rng.uniform(-spread, spread))
+            c = np.mod(a + r * u, L)
+            if free(a) and free(c):
+                pts += [a, c]
+                made += 1
+    n = len(pts)
+    pos = np.zeros((n, 4))
+    pos[:, :3] = pts
+    return inputs.State(pos=pos, vel=np.zeros((n, 4)), image=np.zeros((n, 4), np.int32),
+                        tag=np.arange(n, dtype=np.int32), type=np.zeros(n, np.int32),
+                        box=np.array([[L, L, L]]), offsets=np.array([0, n], np.int64))
+
+
+@pytest.mark.parametrize("w", (1, 2))
+def test_pairs_at_the_fp32_band_ends(w):
+    """Every pair inside r_list is listed and every pair inside r_cut feels
+    its force, in both precisions, also where the FP32 r^2 falls within an
+    ulp or two of the band's rounded ends (a threshold that left a sliver
+    between the FP32 decision and the FP64 re-test dropped such pairs)."""
+    st = band_ends_state(seed=80 + w)
+    L = st.box[0]
+    cb, rb = oracle.neighbors(st.pos, L, 2.8, max_nb=32, method="cells")
+    ref, _, absf = oracle.lj_forces(st.pos, L, 2.5)
+    assert 150 < np.sum(cb) // 2 < 400 and np.sum(absf > 0) > 100
+    for prec in ("fp64", "mixed"):
+        s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, precision=prec, max_nb=32)
+        s.set_tuning(md.KERNEL_PAIR, 128, w)
+        s.set_tuning(md.KERNEL_NLIST, 64, w)
+        s.prepare()
+        counts, rows = (x.cpu().numpy() for x in s.nlist())
+        assert np.array_equal(counts, cb), prec
+        for i in np.nonzero(cb)[0]:
+            assert np.array_equal(np.sort(rows[i, :counts[i]]), rb[i, :cb[i]]), (prec, i)
+        f = s.forces().cpu().numpy()
+        s.check_error()
+        # isolated pairs: a particle feels a force iff its partner is inside r_cut
+        assert np.array_equal(np.linalg.norm(f[:, :3], axis=1) > 0, absf > 0), prec
+        if prec == "fp64":
+            fp64_force_check(f, ref, absf)
+        else:
+            rms, mx = mixed_force_stats(f, ref, absf)
+            assert rms <= 1e-5 and mx <= 1e-3, (rms, mx)
+        s.close()

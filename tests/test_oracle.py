@@ -516,3 +516,115 @@ def test_cell_list_rows_in_a_box_that_is_an_exact_multiple_of_r_list():
     cc, rc = oracle.neighbors(pos, L, rl, method="cells")
     assert cb.tolist() == [1] * 8
     assert np.array_equal(cb, cc) and np.array_equal(rb, rc)
+
+
+# --------------------------------------------------------------------------
+# thermostats: Langevin (BAOAB) and Nose-Hoover (one thermostat, MTK splitting)
+
+def test_langevin_noise_statistics_and_keys():
+    th = np.array([oracle.langevin_noise(t, s, 3) for t in range(4000) for s in (1, 2)])
+    assert th.shape == (8000, 3)
+    assert np.abs(th.mean(0)).max() < 0.04
+    assert np.abs(th.var(0) - 1.0).max() < 0.04
+    assert th.max() < math.sqrt(3) and th.min() > -math.sqrt(3)
+    assert abs(np.corrcoef(th[:, 0], th[:, 1])[0, 1]) < 0.04  # components independent
+    a = oracle.langevin_noise(7, 11, 3)
+    assert not np.array_equal(a, oracle.langevin_noise(8, 11, 3))
+    assert not np.array_equal(a, oracle.langevin_noise(7, 12, 3))
+    assert not np.array_equal(a, oracle.langevin_noise(7, 11, 4))
+
+
+def test_baoab_without_friction_is_velocity_verlet():
+    st = inputs.lj_fluid(864, 0.8442, 1.44, seed=21)
+    L = st.box[0]
+    kw = dict(r_cut=2.5, r_skin=0.3, dt=0.005)
+    a = oracle.run(st.pos, st.vel, st.image, L, 50, **kw)
+    b = oracle.run(st.pos, st.vel, st.image, L, 50, integrator="langevin", gamma=0.0, t_kT=1.0,
+                   t_seed=5, **kw)
+    xa = a["pos"][:, :3] + a["image"][:, :3] * L
+    xb = b["pos"][:, :3] + b["image"][:, :3] * L
+    assert np.max(np.abs(xa - xb)) < 1e-10
+    assert np.max(np.abs(a["vel"] - b["vel"])) < 1e-9
+
+
+def _free_gas(n=3000, L=200.0, seed=22):
+    # particles more than r_cut apart: no pair forces, only the thermostat acts
+    g = np.stack(np.meshgrid(*[np.arange(15)] * 3, indexing="ij"), -1).reshape(-1, 3)[:n]
+    pos = np.zeros((n, 4))
+    pos[:, :3] = (g + 0.5) * (L / 15)
+    return pos, np.zeros((n, 4), np.int32), np.array([L, L, L])
+
+
+def test_langevin_o_step_relaxation_of_free_particles():
+    """Without forces BAOAB's velocities follow the O step exactly:
+    v_n = c^n v_0 + noise, c = exp(-gamma dt), so from rest E[v_n^2] =
+    (1 - c^(2n)) kT/m, and from Maxwell-Boltzmann velocities at kT the
+    autocorrelation is E[v_n v_0] / E[v_0^2] = c^n."""
+    pos, img, L = _free_gas()
+    n = len(pos)
+    gamma, dt, kT, steps = 2.0, 0.01, 1.5, 50
+    c = math.exp(-gamma * dt)
+    kw = dict(r_cut=2.5, r_skin=0.3, dt=dt, integrator="langevin", gamma=gamma, t_kT=kT,
+              t_seed=9, max_nb=8)
+    out = oracle.run(pos, np.zeros((n, 4)), img, L, steps, **kw)
+    v2 = np.mean(out["vel"][:, :3] ** 2)
+    assert v2 == pytest.approx((1 - c ** (2 * steps)) * kT, rel=0.04)
+    v0 = np.zeros((n, 4))
+    v0[:, :3] = np.random.default_rng(1).standard_normal((n, 3)) * math.sqrt(kT)
+    out = oracle.run(pos, v0, img, L, steps, **kw)
+    acf = np.mean(out["vel"][:, :3] * v0[:, :3]) / np.mean(v0[:, :3] ** 2)
+    assert acf == pytest.approx(c ** steps, abs=0.03)
+
+
+def test_langevin_lj_fluid_equipartition():
+    st = inputs.lj_fluid(864, 0.8442, 0.6, seed=23)
+    L = st.box[0]
+    out = oracle.run(st.pos, st.vel, st.image, L, 3000, r_cut=2.5, r_skin=0.3, dt=0.005,
+                     integrator="langevin", gamma=1.0, t_kT=1.2, t_seed=4, thermo_period=10)
+    T = out["thermo"][100:, 4].mean()
+    assert T == pytest.approx(1.2, rel=0.03)
+
+
+def test_nose_hoover_with_a_slow_thermostat_is_velocity_verlet():
+    st = inputs.lj_fluid(864, 0.8442, 1.44, seed=24)
+    L = st.box[0]
+    kw = dict(r_cut=2.5, r_skin=0.3, dt=0.005)
+    a = oracle.run(st.pos, st.vel, st.image, L, 50, **kw)
+    b = oracle.run(st.pos, st.vel, st.image, L, 50, integrator="nose-hoover", tau=1e9, t_kT=1.0,
+                   **kw)
+    xa = a["pos"][:, :3] + a["image"][:, :3] * L
+    xb = b["pos"][:, :3] + b["image"][:, :3] * L
+    assert np.max(np.abs(xa - xb)) < 1e-10
+    assert abs(b["nh_state"][0]) < 1e-15
+
+
+def _nh_run(dt, t_end, n=864, kT=1.3, tau=0.3, seed=25):
+    st = inputs.lj_fluid(n, 0.8442, 0.8, seed=seed)
+    L = st.box[0]
+    g = 3 * n - 3
+    kw = dict(r_cut=2.5, r_skin=0.3, dt=dt, shift_energy=True, integrator="nose-hoover",
+              tau=tau, t_kT=kT, thermo_period=10)
+    state, nh, H, T = (st.pos, st.vel, st.image), np.zeros(2), [], []
+    for k in range(int(round(t_end / (10 * dt)))):
+        out = oracle.run(*state, L, 10, step0=10 * k, nh_state=nh, **kw)
+        state, nh = (out["pos"], out["vel"], out["image"]), out["nh_state"]
+        ke, pe = out["thermo"][-1, 0], out["thermo"][-1, 1]
+        H.append((ke + pe + g * kT * tau * tau * nh[0] ** 2 / 2 + g * kT * nh[1]) / n)
+        T.append(out["thermo"][-1, 4])
+    return np.array(H), np.array(T)
+
+
+def test_nose_hoover_conserved_quantity_and_temperature():
+    """H = KE + PE + g kT tau^2 xi^2 / 2 + g kT eta (g = 3N - 3) is conserved
+    by the Nose-Hoover dynamics; the splitting conserves it up to an error of
+    second order in dt (halving dt divides the largest deviation by about
+    four; a wrong term or coefficient leaves a first-order or constant drift
+    instead).  Started at T = 0.8 with kT = 1.3, so the thermostat does real
+    work; the kinetic temperature then averages to kT."""
+    H1, T1 = _nh_run(0.005, 7.5)
+    H2, _ = _nh_run(0.0025, 7.5)
+    e1, e2 = np.abs(H1 - H1[0]).max(), np.abs(H2 - H2[0]).max()
+    assert 3.0 < e1 / e2 < 5.5, (e1, e2)
+    assert e2 < 2.5e-3
+    assert T1[0] < 1.0  # started cold
+    assert np.mean(T1[40:]) == pytest.approx(1.3, rel=0.04)

@@ -74,12 +74,14 @@ def test_noalloc_rejects_systems_beyond_its_scratch():
     assert e.value.code == 5  # MD_ERR_CELL_GRID
 
 
-def _check_vs_oracle(f_new, pos, box, r_cut):
+def _check_vs_oracle(f_new, pos, box, r_cut, brute=None):
     """The FP64 parity rule of the other GPU tests against the oracle's
     forces: |dF| <= 1e-12 |F| where |F| >= 1e-2 S, else <= 1e-14 S, with S
-    the oracle's sum of pair-force magnitudes (cell-list oracle: O(N))."""
-    nl = oracle.neighbors(pos, box, r_cut, max_nb=128,
-                          method="brute" if len(pos) < 5000 else "cells")
+    the oracle's sum of pair-force magnitudes (all-pairs oracle for small or
+    unwrapped inputs, its cell list otherwise)."""
+    if brute is None:
+        brute = len(pos) < 5000
+    nl = oracle.neighbors(pos, box, r_cut, max_nb=128, method="brute" if brute else "cells")
     ref, _, absf = oracle.lj_forces(pos, box, r_cut, nlist=nl)
     d = np.linalg.norm(f_new[:, :3] - ref[:, :3], axis=1)
     F = np.linalg.norm(ref[:, :3], axis=1)
@@ -127,12 +129,14 @@ def test_noalloc_noncubic_box_and_unwrapped_positions():
     p = torch.as_tensor(st.pos, device="cuda")
     f = md.lj_forces_noalloc(p, st.box[0], 2.5).cpu().numpy()
     _check_vs_oracle(f, st.pos, st.box[0], 2.5)
-    # the same positions shifted by whole box lengths (callers need not wrap)
+    # the positions shifted by whole box lengths (callers need not wrap); the
+    # shifted inputs are rounded (an ulp of ~4 L), so they are compared with
+    # the oracle on the same shifted inputs
     shift = np.random.default_rng(5).integers(-3, 4, (st.n, 3)) * st.box[0]
     q = st.pos.copy()
     q[:, :3] += shift
     fq = md.lj_forces_noalloc(torch.as_tensor(q, device="cuda"), st.box[0], 2.5).cpu().numpy()
-    _check_vs_oracle(fq, st.pos, st.box[0], 2.5)
+    _check_vs_oracle(fq, q, st.box[0], 2.5, brute=True)
 
 
 def test_noalloc_box_an_exact_multiple_of_r_cut():
