@@ -584,6 +584,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
           LJCoeffF f{(float)(48 * eps * s12), (float)(24 * eps * s6), (float)(4 * eps * s12),
                      (float)(4 * eps * s6), (float)vc, 0, 0, 0};
           std::memcpy(coeff.data() + sizeof(LJCoeffF) * c, &f, sizeof(f));
+          if (c == 0) a.lj1f = f;
         } else {
           LJCoeffD d{48 * eps * s12, 24 * eps * s6, 4 * eps * s12, 4 * eps * s6, vc, 0, 0, 0};
           std::memcpy(coeff.data() + sizeof(LJCoeffD) * c, &d, sizeof(d));
@@ -594,6 +595,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
         if (mixed) {
           DPDCoeffF f{(float)A, (float)gamma, (float)srdt, 0};
           std::memcpy(coeff.data() + sizeof(DPDCoeffF) * c, &f, sizeof(f));
+          if (c == 0) a.dpd1f = f;
         } else {
           DPDCoeffD d{A, gamma, srdt, 0};
           std::memcpy(coeff.data() + sizeof(DPDCoeffD) * c, &d, sizeof(d));

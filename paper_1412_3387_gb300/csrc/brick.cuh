@@ -290,23 +290,27 @@ __device__ __forceinline__ void desc_fetch(const KArgs &a, long long b, BrickDes
   for (int k = threadIdx.x; k < (int)(sizeof(BrickDesc) / 16); k += blockDim.x) d[k] = __ldg(src + k);
 }
 
-// Warp 0 issues the copies of a brick's stage (positions, and velocities if
-// vel4 is given) as one bulk copy per stage cell (lanes over cells), counted
-// on `bar`; a brick served from global memory only arrives.  The buffer's
-// previous readers and writers fenced and synchronised before this.
+// Issues the copies of a brick's stage (positions, and velocities if vel4 is
+// given), counted on `bar`: the block's warps share the 64 stage cells (warp
+// w takes cells w, w + C, ...), and the two cells of each stage row that
+// belong to the brick itself (stage x = 1, 2), adjacent in cell-list order,
+// go as one copy.  A brick served from global memory only arrives.  The
+// buffer's previous readers and writers fenced and synchronised before this.
+// (The arrival may follow some copies' completion: the phase cannot complete
+// before its one arrival.)
 __device__ __forceinline__ void stage_issue(const KArgs &a, const BrickDesc &d, float4 *pos,
                                             float4 *vel4, uint64_t *bar, int cap) {
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
   const bool staged = d.off[64] <= cap;
-  if (lane == 0)
+  if (threadIdx.x == 0)
     mbar_arrive_expect_tx(bar, staged ? (uint32_t)d.off[64] * 16u * (vel4 ? 2u : 1u) : 0u);
-  __syncwarp();
   if (!staged) return;
-#pragma unroll
-  for (int k = 0; k < 2; k++) {
-    const int s = lane + 32 * k;
-    const int o = d.off[s], n = d.off[s + 1] - o, st = d.start[s];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, C = blockDim.x >> 5;
+  for (int s = warp + C * lane; s < kStageCells; s += 32 * C) {
+    const int sx = s & 3;
+    int o = d.off[s], n = d.off[s + 1] - o;
+    const int st = d.start[s];
+    if (sx == 2 && d.start[s - 1] + (o - d.off[s - 1]) == st) continue;  // sent with its left neighbour
+    if (sx == 1 && st + n == d.start[s + 1]) n += d.off[s + 2] - d.off[s + 1];
     if (n > 0) {
       bulk_g2s(pos + 1 + o, a.pos4f + st, 16u * (uint32_t)n, bar);
       if (vel4) bulk_g2s(vel4 + 1 + o, a.vel4f + st, 16u * (uint32_t)n, bar);

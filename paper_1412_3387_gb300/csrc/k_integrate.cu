@@ -109,12 +109,14 @@ __device__ __forceinline__ void langevin_theta(int32_t tag, uint64_t step, uint6
 // hk = dt / (2m); or dt / m when the previous step's second half-kick was
 // left out (inside a run): v(t - 1/2) -> v(t + 1/2) = v(t - 1/2) + dt F(t) / m,
 // the same velocity-Verlet step written as one kick.
-__global__ void k_integrate1(KArgs a, double hk) {
+// Grid-stride: a bounded grid keeps the end-of-kernel ticket (one fenced
+// atomic per block) cheap.
+__global__ void __launch_bounds__(256) k_integrate1(KArgs a, double hk) {
   __shared__ int is_last;
   const int64_t t = a.ds->step;
   const int par = (int)((t + 1) & 1);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < a.n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
     const int r = replica_of(a, i);
     const Rep &rp = a.rep[r];
     double4 x = ld_d4_plain(a.pos + i);
@@ -552,8 +554,10 @@ __global__ void k_philox(const uint32_t *in, uint32_t *out, int64_t n) {
 }  // namespace
 
 cudaError_t launch_integrate1(const KArgs &a, cudaStream_t st, bool fold_kick) {
-  // the step counter must advance even for an empty system
-  k_integrate1<<<blocks_for(a.n > 0 ? a.n : 1, 256), 256, 0, st>>>(
+  // the step counter must advance even for an empty system; at most 8
+  // blocks per SM (152 SMs), grid-stride beyond that
+  const unsigned need = blocks_for(a.n > 0 ? a.n : 1, 256);
+  k_integrate1<<<need < 152u * 8u ? need : 152u * 8u, 256, 0, st>>>(
       a, fold_kick ? 2.0 * a.half_dt_m : a.half_dt_m);
   return cudaGetLastError();
 }

@@ -55,6 +55,7 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
   // re-test: bthr is the larger exact distance of the rounded band ends from
   // r_list^2, so |r^2 - r_list^2| <= bthr for every r^2 in the band
   const float bthr = fmaxf(a.rl2f - lo2, hi2 - a.rl2f);
+  const float rl2f = a.rl2f;  // a local: read in the candidate loop
   const uint64_t oixy = pack2(oi.x, oi.y);
   const int max_nb = a.max_nb;
   // the pair kernel's row layout: groups of Pp = 32 / Wp particles, tiles of
@@ -158,7 +159,7 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
       unsigned m = 0u;       // bit u: candidate x0 + u is a neighbour
 #pragma unroll
       for (int u = 0; u < U; u++) {
-        bmin = fminf(bmin, fabsf(r2u[u] - a.rl2f));
+        bmin = fminf(bmin, fabsf(r2u[u] - rl2f));
         m |= (r2u[u] < lo2 ? 1u : 0u) << u;
       }
       if (__any_sync(FULL, bmin <= bthr)) {

@@ -143,6 +143,11 @@ struct KArgs {
   int32_t *s_tag, *s_type;
   float4 *s_oref;
   const void *coeff;   // LJCoeff* / DPDCoeff* [ntypes^2], precision-matched
+  // the single type pair's FP32 coefficients, as kernel parameters: the
+  // mixed pair loops take them as constant operands instead of re-loading
+  // them from memory
+  LJCoeffF lj1f;
+  DPDCoeffF dpd1f;
   // parameters
   int32_t max_nb;        // a multiple of 32
   int32_t w_store_log2;  // neighbour-list tile width (pair kernel's w)

@@ -243,7 +243,10 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
   const int p = hs.p;
   const int32_t i = ident ? p : __ldg(a.cell_idx + p);
   const StageSrc<DIRECT> src{a, d, rp, smem_u32(spos), smem_u32(svel)};
-  const float4 oi = src.pos((uint32_t)(hs.slot + 1));
+  // the home particle's stage coordinates, read once (a volatile load: the
+  // compiler keeps the value instead of re-reading it inside the loop)
+  const float4 oi = DIRECT ? src.pos((uint32_t)(hs.slot + 1))
+                           : lds4(smem_u32(spos) + 16u * (uint32_t)(hs.slot + 1));
   const int pg = d.hstart + j * P;
   const int NB = __ldg(a.nl_tiles + pg) / V;        // blocks of V tiles
   const int bstride = (FULLG ? 32 : pj * W) * V;    // entries per block
@@ -264,8 +267,8 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
     mp.rc2_hi = a.rc2f + rp.band;
     mp.inv_rc = (float)(1.0 / a.r_cut);
     if (ONE) {
-      if (POT == kLJ) mp.lj0 = reinterpret_cast<const LJCoeffF *>(a.coeff)[0];
-      else mp.dp0 = reinterpret_cast<const DPDCoeffF *>(a.coeff)[0];
+      if (POT == kLJ) mp.lj0 = a.lj1f;
+      else mp.dp0 = a.dpd1f;
     }
     if (POT == kDPD) {
       mp.vi4 = src.vel((uint32_t)(hs.slot + 1));
@@ -316,6 +319,18 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
     }
   };
 
+  // Everything the hot loop reads is a plain local here: a field read
+  // through a reference member of a helper struct (mp.a, src.a) would be a
+  // memory load from the parameter buffer inside the loop.
+  const LJCoeffF lj = a.lj1f;
+  const DPDCoeffF dc = a.dpd1f;
+  const int ntypes = a.ntypes, ti = cell_type(__float_as_uint(oi.w));
+  const void *coeff = a.coeff;
+  const float inv_rc = (float)(1.0 / a.r_cut), r_cut_f = (float)a.r_cut;
+  const uint64_t seed = a.seed;
+  const float4 vi4 = MIXED && POT == kDPD ? mp.vi4 : make_float4(0.f, 0.f, 0.f, 0.f);
+  const int32_t tag_i = MIXED && POT == kDPD ? mp.tag_i : 0;
+
   // the V entries of one block, mixed precision: group sums (gx, gy, gz),
   // smallest |r^2 - r_cut^2| in bmin
   auto mixed_block = [&](const Word &w, float &gx, float &gy, float &gz, float &bmin) {
@@ -329,27 +344,27 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
       bmin = fminf(bmin, fabsf(r2 - rc2f));
       float fr, en = 0.f;
       if (POT == kLJ) {
-        const LJCoeffF c = ONE ? mp.lj0
-                               : reinterpret_cast<const LJCoeffF *>(a.coeff)[
-                                     mp.ti * a.ntypes + cell_type(__float_as_uint(ojw))];
+        const LJCoeffF c = ONE ? lj
+                               : reinterpret_cast<const LJCoeffF *>(coeff)[
+                                     ti * ntypes + cell_type(__float_as_uint(ojw))];
         const float r2i = __fdividef(1.0f, r2);
         const float r6 = r2i * r2i * r2i;
         fr = in ? r2i * r6 * (c.lj1 * r6 - c.lj2) : 0.f;
         if (ENERGY) en = in ? r6 * (c.lj3 * r6 - c.lj4) - c.vshift : 0.f;
       } else {
-        const DPDCoeffF c = ONE ? mp.dp0
-                                : reinterpret_cast<const DPDCoeffF *>(a.coeff)[
-                                      mp.ti * a.ntypes + cell_type(__float_as_uint(ojw))];
+        const DPDCoeffF c = ONE ? dc
+                                : reinterpret_cast<const DPDCoeffF *>(coeff)[
+                                      ti * ntypes + cell_type(__float_as_uint(ojw))];
         const float4 vj = DIRECT ? src.vel(e) : reinterpret_cast<const float4 *>(svel)[e];
         const float rinv = rsqrtf(r2);
-        const float wgt = fmaf(-r2 * rinv, mp.inv_rc, 1.f);
-        const float dot = dx * (mp.vi4.x - vj.x) + dy * (mp.vi4.y - vj.y) + dz * (mp.vi4.z - vj.z);
-        const uint32_t word = dpd_word(mp.tag_i, __float_as_int(vj.w), step, a.seed);
+        const float wgt = fmaf(-r2 * rinv, inv_rc, 1.f);
+        const float dot = dx * (vi4.x - vj.x) + dy * (vi4.y - vj.y) + dz * (vi4.z - vj.z);
+        const uint32_t word = dpd_word(tag_i, __float_as_int(vj.w), step, seed);
         const float uu = ((float)(word >> 8) + 0.5f) * 5.9604644775390625e-08f;  // 2^-24
         const float theta = 1.7320508075688772f * (2.f * uu - 1.f);
         const float fmag = c.A * wgt - c.gamma * wgt * wgt * dot * rinv + c.sigma_rdt * wgt * theta;
         fr = in ? fmag * rinv : 0.f;
-        if (ENERGY) en = in ? 0.5f * c.A * (float)a.r_cut * wgt * wgt : 0.f;
+        if (ENERGY) en = in ? 0.5f * c.A * r_cut_f * wgt * wgt : 0.f;
       }
       gx = fmaf(fr, dx, gx);
       gy = fmaf(fr, dy, gy);
