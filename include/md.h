@@ -50,7 +50,8 @@ typedef enum {
     MD_ERR_WORKSPACE_TOO_SMALL = 3,  /* ws_bytes < md_workspace_size() */
     MD_ERR_NLIST_OVERFLOW = 4,       /* a neighbour row exceeded max_nb; detail = needed */
     MD_ERR_CELL_GRID = 5,            /* fewer than 3 cells per box edge */
-    MD_ERR_NONFINITE = 6,            /* non-finite position after integration */
+    MD_ERR_NONFINITE = 6,            /* non-finite position after integration, or a finite
+                                        one the periodic wrap cannot bring into the box */
     MD_ERR_CELL_OVERFLOW = 7,        /* a cell held more particles than can be ordered */
     MD_ERR_STATE = 8,                /* call not valid in the current state */
     MD_ERR_TIMEOUT = 9               /* a kernel's wait for its own shared-memory copies gave
@@ -280,7 +281,8 @@ md_status md_get_step(md_system *s, int64_t *step); /* synchronises */
  * the paper (error reporting of this interface).  Returns MD_OK or the first
  * recorded error, in this order of precedence: MD_ERR_NLIST_OVERFLOW
  * (*detail = the max_nb needed), MD_ERR_NONFINITE (*detail = the index of a
- * particle with a non-finite position), MD_ERR_CELL_OVERFLOW, MD_ERR_STATE (a
+ * particle with a non-finite position, or a finite one more than 1e9 box
+ * lengths outside the box), MD_ERR_CELL_OVERFLOW, MD_ERR_STATE (a
  * force evaluation found its replica's list stale and computed nothing),
  * MD_ERR_TIMEOUT.  The word is not cleared.  detail may be NULL. */
 md_status md_poll_error(md_system *s, int64_t *detail);

@@ -236,6 +236,14 @@ __device__ __forceinline__ uint64_t sub_f32x2(uint64_t a, uint64_t b) {
   return d;
 }
 
+// 1 / x by the hardware approximation (one instruction; about one ulp of
+// relative error, and +inf gives +0).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ float lds1(uint32_t addr) {
   float v;
   asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
@@ -346,13 +354,34 @@ __device__ __forceinline__ void stage_shift_all(const KArgs &a, const BrickDesc 
                                                 int cap) {
   if (d.off[64] > cap) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, C = blockDim.x >> 5;
-  const Rep &rp = a.rep[d.r];
-  for (int s = warp; s < kStageCells; s += C) {
-    const int o = d.off[s], n = d.off[s + 1] - o;
-    const float3 h = stage_shift(rp, s, d.bc);
-    for (int m = lane; m < n; m += 32) {
-      const float4 v = pos[1 + o + m];
-      pos[1 + o + m] = make_float4(v.x + h.x, v.y + h.y, v.z + h.z, v.w);
+  // the brick's twelve shifts, one per lane 4 ax + s (ax = axis, s = stage
+  // coordinate), computed once and broadcast to the cells by shuffles
+  float tab = 0.f;
+  if (lane < 12) {
+    const int ax = lane >> 2;
+    tab = stage_shift1(a.rep[d.r], ax, lane & 3, (d.bc >> (10 * ax)) & 1023);
+  }
+  auto shift_of = [&](int s) {
+    float3 h;
+    h.x = __shfl_sync(0xffffffffu, tab, s & 3);
+    h.y = __shfl_sync(0xffffffffu, tab, 4 + ((s >> 2) & 3));
+    h.z = __shfl_sync(0xffffffffu, tab, 8 + (s >> 4));
+    return h;
+  };
+  // two cells per pass (s and s + C), both loads ahead of both stores
+  float4 *const p1 = pos + 1;
+  for (int s = warp; s < kStageCells; s += 2 * C) {
+    const int t = s + C < kStageCells ? s + C : s;
+    const int oa = d.off[s], na = d.off[s + 1] - oa;
+    const int ob = d.off[t], nb = t != s ? d.off[t + 1] - ob : 0;
+    const float3 ha = shift_of(s), hb = shift_of(t);
+    const int nm = na > nb ? na : nb;
+    for (int m = lane; m < nm; m += 32) {
+      float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
+      if (m < na) va = p1[oa + m];
+      if (m < nb) vb = p1[ob + m];
+      if (m < na) p1[oa + m] = make_float4(va.x + ha.x, va.y + ha.y, va.z + ha.z, va.w);
+      if (m < nb) p1[ob + m] = make_float4(vb.x + hb.x, vb.y + hb.y, vb.z + hb.z, vb.w);
     }
   }
 }

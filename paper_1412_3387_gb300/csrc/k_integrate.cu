@@ -160,7 +160,11 @@ __global__ void __launch_bounds__(256) k_integrate1(KArgs a, double hk) {
     const float ex = o.x - ref.x, ey = o.y - ref.y, ez = o.z - ref.z;
     const float d2 = ex * ex + ey * ey + ez * ez;
     if (!(d2 <= a.disp2_f)) a.rebuild[2 * r + par] = 1;  // NaN also triggers
-    if (!finite_bits(x.x) || !finite_bits(x.y) || !finite_bits(x.z)) {
+    // a non-finite position, or a finite one the wrap could not bring into
+    // the box (more than 1e9 box lengths out): the step is invalid
+    if (outside_box(x.x, __double_as_longlong(rp.L[0])) ||
+        outside_box(x.y, __double_as_longlong(rp.L[1])) ||
+        outside_box(x.z, __double_as_longlong(rp.L[2]))) {
       if (atomicOr(&a.ds->error, kErrNonfinite) == 0u) a.ds->error_detail = i;
     }
     if (a.vel4f) a.vel4f[p] = make_float4((float)v.x, (float)v.y, (float)v.z, __int_as_float(a.tag[i]));

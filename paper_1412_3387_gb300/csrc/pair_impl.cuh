@@ -100,7 +100,7 @@ struct MixedPair {
     float fr, v = 0.f;
     if (POT == kLJ) {
       const LJCoeffF c = ONE ? lj0 : reinterpret_cast<const LJCoeffF *>(a.coeff)[cidx];
-      const float r2i = __fdividef(1.0f, r2);
+      const float r2i = rcp_approx(r2);
       const float r6 = r2i * r2i * r2i;
       fr = r2i * r6 * (c.lj1 * r6 - c.lj2);
       if (ENERGY) v = r6 * (c.lj3 * r6 - c.lj4) - c.vshift;
@@ -347,7 +347,7 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
         const LJCoeffF c = ONE ? lj
                                : reinterpret_cast<const LJCoeffF *>(coeff)[
                                      ti * ntypes + cell_type(__float_as_uint(ojw))];
-        const float r2i = __fdividef(1.0f, r2);
+        const float r2i = rcp_approx(r2);
         const float r6 = r2i * r2i * r2i;
         fr = in ? r2i * r6 * (c.lj1 * r6 - c.lj2) : 0.f;
         if (ENERGY) en = in ? r6 * (c.lj3 * r6 - c.lj4) - c.vshift : 0.f;

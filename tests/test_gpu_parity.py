@@ -481,6 +481,30 @@ def test_nonfinite_position_is_reported_and_stops_list_builds():
     assert not np.isfinite(pos[123, :3]).all()
 
 
+def test_position_beyond_the_wrap_is_reported():
+    """Finite velocities far too large for the box (injected on the host): a
+    particle that moves 1e5 box lengths in one step is wrapped back with its
+    image count; one that moves more than 1e9 box lengths cannot be wrapped,
+    and the first integration half flags it as an invalid position with its
+    index (the error word, not a fault); later list builds are skipped."""
+    import time
+    st = lj_state(n=4000)
+    L = float(st.box[0, 0])
+    st.vel[77, 0] = 1e5 * L / 0.005  # wraps
+    st.vel[78, 1] = -1e300           # cannot wrap
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, graph_steps=100, thermo_period=100)
+    s.prepare()
+    t0 = time.perf_counter()
+    s.run(200)
+    code, detail = s.poll_error()
+    assert time.perf_counter() - t0 < 30.0
+    assert code == 6, (code, detail)
+    pos = s.state_numpy()["pos"]
+    assert 0 <= detail < st.n
+    p = pos[detail, :3]
+    assert not (np.isfinite(p).all() and (p >= 0).all() and (p < L).all()), p
+
+
 def oracle_drifts():
     """The CPU oracle's own drift on the same eight seeded trajectories
     (tests/golden/nve_drift_oracle.txt, written by make_nve_drift_oracle.py)."""
