@@ -68,6 +68,10 @@ def lib():
                 "orc_neighbors_brute": (I32, [I64, P, P, D, P, P, I32]),
                 "orc_neighbors_cells": (I32, [I64, P, P, D, P, P, I32]),
                 "orc_lj_pair": (D, [D, D, D, P]),
+                "orc_pair_ncoeff": (I32, [I32]),
+                "orc_pair_eval": (D, [I32, D, P, P]),
+                "orc_pair_forces_brute": (None, [I32, I64, P, P, P, D, I32, P, I32, P, P, P]),
+                "orc_pair_forces_nlist": (None, [I32, I64, P, P, P, D, I32, P, I32, P, P, I32, P, P, P]),
                 "orc_lj_forces_brute": (None, [I64, P, P, P, D, I32, P, I32, P, P, P]),
                 "orc_lj_forces_nlist": (None, [I64, P, P, P, D, I32, P, I32, P, P, I32, P, P, P]),
                 "orc_philox4x32_10": (None, [P, P, P]),
@@ -146,9 +150,50 @@ def lj_pair(r2, eps=1.0, sigma=1.0):
     return fr, v.value
 
 
-def _coeff(coeff, ntypes):
-    c = np.ascontiguousarray(coeff, np.float64).reshape(ntypes, ntypes, 2)
+def _coeff(coeff, ntypes, k=2):
+    c = np.ascontiguousarray(coeff, np.float64).reshape(ntypes, ntypes, k)
     return c
+
+
+# pair kinds (oracle.h): coefficients per ordered type pair
+PAIR_KINDS = {"lj": 0, "dpd": 1, "gauss": 2, "morse": 3, "yukawa": 4}
+
+
+def pair_ncoeff(pair):
+    return int(lib().orc_pair_ncoeff(PAIR_KINDS[pair]))
+
+
+def pair_eval(pair, r2, c):
+    """(-dV/dr / r, V) of one pair at r^2 (kinds lj, gauss, morse, yukawa)."""
+    v = C.c_double()
+    cc = np.ascontiguousarray(c, np.float64)
+    fr = lib().orc_pair_eval(PAIR_KINDS[pair], float(r2), _p(cc), C.byref(v))
+    return fr, v.value
+
+
+def pair_forces(pair, pos, L, r_cut, coeff, type=None, shift_energy=False, nlist=None):
+    """(force[N,4], virial[N,6], absf[N]) of kind lj, gauss, morse or yukawa,
+    from brute force or given rows."""
+    kind = PAIR_KINDS[pair]
+    k = pair_ncoeff(pair)
+    pos = _f64(pos)
+    n = pos.shape[0]
+    ntypes = int(round(np.sqrt(np.asarray(coeff, np.float64).size / k)))
+    c = _coeff(coeff, ntypes, k)
+    t = _i32(np.zeros(n) if type is None else type)
+    force = np.zeros((n, 4))
+    virial = np.zeros((n, 6))
+    absf = np.zeros(n)
+    if nlist is None:
+        lib().orc_pair_forces_brute(kind, n, _p(pos), _p(t), _p(_box(L)), float(r_cut), ntypes,
+                                    _p(c), int(shift_energy), _p(force), _p(virial), _p(absf))
+    else:
+        counts, rows = nlist
+        counts, rows = _i32(counts), _i32(rows)
+        lib().orc_pair_forces_nlist(kind, n, _p(pos), _p(t), _p(_box(L)), float(r_cut), ntypes,
+                                    _p(c), int(shift_energy), _p(counts), _p(rows),
+                                    rows.shape[1], _p(force), _p(virial), _p(absf))
+    return force, virial, absf
 
 
 def lj_forces(pos, L, r_cut, coeff=((1.0, 1.0),), type=None, shift_energy=False,
@@ -300,8 +345,9 @@ def run(pos, vel, image, L, n_steps, *, r_cut, r_skin, dt, pair="lj", type=None,
     pos, vel = _f64(pos).copy(), _f64(vel).copy()
     image = _i32(image).copy()
     n = pos.shape[0]
-    ntypes = int(round(np.sqrt(np.asarray(coeff, np.float64).size / 2)))
-    c = _coeff(coeff, ntypes)
+    k = pair_ncoeff(pair)
+    ntypes = int(round(np.sqrt(np.asarray(coeff, np.float64).size / k)))
+    c = _coeff(coeff, ntypes, k)
     t = _i32(np.zeros(n) if type is None else type)
     g = _i32(np.arange(n) if tag is None else tag)
     b = _i32(np.zeros((0, 2)) if bonds is None else bonds).reshape(-1, 2)
@@ -310,7 +356,7 @@ def run(pos, vel, image, L, n_steps, *, r_cut, r_skin, dt, pair="lj", type=None,
     p.L = (C.c_double * 3)(*_box(L).tolist())
     p.r_cut, p.r_skin, p.dt, p.mass, p.kT = r_cut, r_skin, dt, mass, kT
     p.seed = int(seed)
-    p.pair = 0 if pair == "lj" else 1
+    p.pair = PAIR_KINDS[pair]
     p.ntypes = ntypes
     p.coeff = c.ctypes.data
     p.shift_energy = int(shift_energy)

@@ -218,6 +218,96 @@ static void lj_one(pacc_t *a, const double *d, double r2, int32_t ti, int32_t tj
     pacc_pair(a, d, fr, v);
 }
 
+int32_t orc_pair_ncoeff(int32_t kind) { return kind == 3 ? 3 : 2; }
+
+/* Gaussian: V = eps e^(-r^2 / 2 sigma^2), -dV/dr = (r / sigma^2) V. */
+static double gauss_pair(double r2, double eps, double sigma, double *v) {
+    *v = eps * exp(-r2 / (2.0 * sigma * sigma));
+    return *v / (sigma * sigma);
+}
+
+/* Morse: with x = e^(-alpha (r - r0)), V = D0 (x^2 - 2 x) and
+ * -dV/dr = 2 D0 alpha (x^2 - x). */
+static double morse_pair(double r2, double d0, double alpha, double r0, double *v) {
+    double r = sqrt(r2);
+    double x = exp(-alpha * (r - r0));
+    *v = d0 * (x * x - 2.0 * x);
+    return 2.0 * d0 * alpha * (x * x - x) / r;
+}
+
+/* Yukawa: V = eps e^(-kappa r) / r, -dV/dr = V (1 + kappa r) / r. */
+static double yukawa_pair(double r2, double eps, double kappa, double *v) {
+    double r = sqrt(r2);
+    *v = eps * exp(-kappa * r) / r;
+    return *v * (1.0 + kappa * r) / r2;
+}
+
+double orc_pair_eval(int32_t kind, double r2, const double *c, double *v) {
+    switch (kind) {
+        case 0: return orc_lj_pair(r2, c[0], c[1], v);
+        case 2: return gauss_pair(r2, c[0], c[1], v);
+        case 3: return morse_pair(r2, c[0], c[1], c[2], v);
+        case 4: return yukawa_pair(r2, c[0], c[1], v);
+        default: *v = 0.0; return 0.0;
+    }
+}
+
+static void pair_one(pacc_t *a, int32_t kind, const double *d, double r2, int32_t ti,
+                     int32_t tj, int32_t ntypes, const double *coeff, double r_cut,
+                     int32_t shift_energy) {
+    const double *c = coeff + (size_t)orc_pair_ncoeff(kind) * (size_t)(ti * ntypes + tj);
+    double v;
+    double fr = orc_pair_eval(kind, r2, c, &v);
+    if (shift_energy) {
+        double vc;
+        orc_pair_eval(kind, r_cut * r_cut, c, &vc);
+        v -= vc;
+    }
+    pacc_pair(a, d, fr, v);
+}
+
+void orc_pair_forces_brute(int32_t kind, int64_t n, const double *pos, const int32_t *type,
+                           const double *L, double r_cut, int32_t ntypes,
+                           const double *coeff, int32_t shift_energy,
+                           double *force, double *virial, double *absf) {
+    double rc2 = r_cut * r_cut;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++) {
+        pacc_t a;
+        pacc_clear(&a);
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double d[3];
+            double r2 = separation(pos + 4 * i, pos + 4 * j, L, d);
+            if (r2 < rc2)
+                pair_one(&a, kind, d, r2, type[i], type[j], ntypes, coeff, r_cut, shift_energy);
+        }
+        pacc_store(&a, i, force, virial, absf);
+    }
+}
+
+void orc_pair_forces_nlist(int32_t kind, int64_t n, const double *pos, const int32_t *type,
+                           const double *L, double r_cut, int32_t ntypes,
+                           const double *coeff, int32_t shift_energy,
+                           const int32_t *counts, const int32_t *rows,
+                           int32_t max_nb, double *force, double *virial,
+                           double *absf) {
+    double rc2 = r_cut * r_cut;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++) {
+        pacc_t a;
+        pacc_clear(&a);
+        for (int32_t k = 0; k < counts[i] && k < max_nb; k++) {
+            int64_t j = rows[i * max_nb + k];
+            double d[3];
+            double r2 = separation(pos + 4 * i, pos + 4 * j, L, d);
+            if (r2 < rc2)
+                pair_one(&a, kind, d, r2, type[i], type[j], ntypes, coeff, r_cut, shift_energy);
+        }
+        pacc_store(&a, i, force, virial, absf);
+    }
+}
+
 void orc_lj_forces_brute(int64_t n, const double *pos, const int32_t *type,
                          const double *L, double r_cut, int32_t ntypes,
                          const double *coeff, int32_t shift_energy,
@@ -606,9 +696,9 @@ static void compute_forces(int64_t n, const double *pos, const double *vel,
                            const orc_params *p, uint64_t step,
                            const int32_t *counts, const int32_t *rows,
                            double *force, double *virial) {
-    if (p->pair == 0)
-        orc_lj_forces_nlist(n, pos, type, p->L, p->r_cut, p->ntypes, p->coeff,
-                            p->shift_energy, counts, rows, p->max_nb, force, virial, NULL);
+    if (p->pair != 1)
+        orc_pair_forces_nlist(p->pair, n, pos, type, p->L, p->r_cut, p->ntypes, p->coeff,
+                              p->shift_energy, counts, rows, p->max_nb, force, virial, NULL);
     else
         orc_dpd_forces_nlist(n, pos, vel, type, tag, p->L, p->r_cut, p->ntypes, p->coeff,
                              p->kT, p->dt, step, p->seed, counts, rows, p->max_nb, force,

@@ -79,6 +79,30 @@ void orc_lj_forces_nlist(int64_t n, const double *pos, const int32_t *type,
                          int32_t max_nb, double *force, double *virial,
                          double *absf);
 
+/* Pair kinds: 0 = LJ (eps, sigma), 1 = DPD (A, gamma), and the other
+ * pair potentials of Sec. 3's list in their textbook forms:
+ *   2 = Gaussian (eps, sigma):   V = eps exp(-r^2 / (2 sigma^2))
+ *   3 = Morse (D0, alpha, r0):   V = D0 [exp(-2 alpha (r - r0)) - 2 exp(-alpha (r - r0))]
+ *   4 = Yukawa (eps, kappa):     V = eps exp(-kappa r) / r
+ * Coefficients per ordered type pair, orc_pair_ncoeff(kind) doubles each. */
+int32_t orc_pair_ncoeff(int32_t kind);
+
+/* Potential of kind 0, 2, 3 or 4 at r^2 with coefficients c: returns
+ * -dV/dr / r (the factor of d = x_i - x_j in f_ij), writes V(r). */
+double orc_pair_eval(int32_t kind, double r2, const double *c, double *v);
+
+/* As orc_lj_forces_brute / orc_lj_forces_nlist for any kind 0, 2, 3, 4. */
+void orc_pair_forces_brute(int32_t kind, int64_t n, const double *pos, const int32_t *type,
+                           const double *L, double r_cut, int32_t ntypes,
+                           const double *coeff, int32_t shift_energy,
+                           double *force, double *virial, double *absf);
+void orc_pair_forces_nlist(int32_t kind, int64_t n, const double *pos, const int32_t *type,
+                           const double *L, double r_cut, int32_t ntypes,
+                           const double *coeff, int32_t shift_energy,
+                           const int32_t *counts, const int32_t *rows,
+                           int32_t max_nb, double *force, double *virial,
+                           double *absf);
+
 /* Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11). */
 void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out);
 
@@ -166,7 +190,7 @@ typedef struct {
     double L[3];
     double r_cut, r_skin, dt, mass, kT;
     uint64_t seed;
-    int32_t pair;          /* 0 = LJ, 1 = DPD */
+    int32_t pair;          /* pair kind (orc_pair_ncoeff) */
     int32_t ntypes;
     const double *coeff;
     int32_t shift_energy;

@@ -107,6 +107,115 @@ def test_lj_newton_third_law_and_shift():
     assert np.allclose(fs[:, 3], f[:, 3] - 0.5 * counts * vc, rtol=1e-12, atol=1e-12)
 
 
+# --------------------------------------------------------------------------
+# Gaussian, Morse and Yukawa pairs (Sec. 3 lists them; textbook forms)
+
+def test_gauss_morse_yukawa_special_values():
+    """Values the definitions fix: the Gaussian's height eps at r -> 0 and half
+    height at r = sigma sqrt(2 ln 2), its force eps/sigma e^-1/2 at r = sigma;
+    the Morse minimum -D0 at r0 with zero force, its zero at r0 - ln2/alpha
+    and -3 D0 / 4 at r0 + ln2/alpha; Yukawa with kappa = 0 is Coulomb
+    (V = eps/r, |F| = eps/r^2), and eps kappa / e at r = 1/kappa."""
+    eps, sig = 1.7, 0.8
+    fr, v = oracle.pair_eval("gauss", 1e-300, [eps, sig])
+    assert v == pytest.approx(eps, rel=1e-15)
+    fr, v = oracle.pair_eval("gauss", 2 * math.log(2) * sig * sig, [eps, sig])
+    assert v == pytest.approx(eps / 2, rel=1e-14)
+    fr, v = oracle.pair_eval("gauss", sig * sig, [eps, sig])
+    assert fr * sig == pytest.approx(eps / sig * math.exp(-0.5), rel=1e-14)
+
+    d0, al, r0 = 2.5, 1.3, 1.1
+    fr, v = oracle.pair_eval("morse", r0 * r0, [d0, al, r0])
+    assert v == pytest.approx(-d0, rel=1e-15) and abs(fr) < 1e-15
+    fr, v = oracle.pair_eval("morse", (r0 - math.log(2) / al) ** 2, [d0, al, r0])
+    assert abs(v) < 1e-14 and fr > 0  # repulsive inside the minimum
+    fr, v = oracle.pair_eval("morse", (r0 + math.log(2) / al) ** 2, [d0, al, r0])
+    assert v == pytest.approx(-0.75 * d0, rel=1e-14) and fr < 0
+
+    for r in (0.5, 1.0, 2.3):
+        fr, v = oracle.pair_eval("yukawa", r * r, [eps, 0.0])
+        assert v == pytest.approx(eps / r, rel=1e-15)
+        assert fr * r == pytest.approx(eps / r ** 2, rel=1e-14)
+    kap = 0.7
+    fr, v = oracle.pair_eval("yukawa", 1.0 / kap ** 2, [eps, kap])
+    assert v == pytest.approx(eps * kap / math.e, rel=1e-14)
+
+
+@pytest.mark.parametrize("pair,c", [("gauss", [1.3, 0.9]), ("morse", [2.0, 1.7, 1.05]),
+                                    ("yukawa", [0.8, 1.4]), ("lj", [1.0, 1.0])])
+def test_pair_force_is_minus_dV_dr(pair, c):
+    """-dV/dr by central differences of the oracle's own V equals the force
+    factor times r (a wrong sign, power or factor in either fails)."""
+    for r in (0.85, 1.0, 1.37, 2.2):
+        h = 1e-5
+        _, vm = oracle.pair_eval(pair, (r - h) ** 2, c)
+        _, vp = oracle.pair_eval(pair, (r + h) ** 2, c)
+        fr, _ = oracle.pair_eval(pair, r * r, c)
+        assert fr * r == pytest.approx((vm - vp) / (2 * h), rel=1e-7, abs=1e-9)
+
+
+def test_morse_dimer_oscillation_period():
+    """Two Morse particles near r0 oscillate with the harmonic period
+    2 pi sqrt(mu / k), k = V''(r0) = 2 D0 alpha^2, mu = m/2 (small amplitude),
+    through the oracle's MD loop (pair kind dispatch, force sign)."""
+    d0, al, r0 = 1.0, 1.5, 1.2
+    L = 12.0
+    pos = np.array([[5.0, 6.0, 6.0, 0.0], [5.0 + r0 + 0.01, 6.0, 6.0, 0.0]])
+    vel = np.zeros((2, 4))
+    img = np.zeros((2, 4), np.int32)
+    dt, steps = 0.002, 3000
+    k = 2 * d0 * al * al
+    period = 2 * math.pi * math.sqrt(0.5 / k)
+    seps = []
+    p, v, im = pos, vel, img
+    for _ in range(steps // 10):
+        out = oracle.run(p, v, im, L, 10, r_cut=3.0, r_skin=0.3, dt=dt, pair="morse",
+                         coeff=[[d0, al, r0]], max_nb=8)
+        p, v, im = out["pos"], out["vel"], out["image"]
+        seps.append(p[1, 0] - p[0, 0] - r0)
+    seps = np.array(seps)
+    t = dt * 10 * np.arange(1, len(seps) + 1)
+    up = [t[i] for i in range(1, len(seps)) if seps[i - 1] < 0 <= seps[i]]
+    measured = np.mean(np.diff(up))
+    assert measured == pytest.approx(period, rel=0.01)
+
+
+@pytest.mark.parametrize("pair,c,r_cut", [("gauss", [1.0, 1.0], 2.6), ("morse", [1.0, 2.0, 1.1], 2.6),
+                                          ("yukawa", [1.0, 1.0], 2.6)])
+def test_new_pairs_fcc_lattice_sum(pair, c, r_cut):
+    """Brute-force sums on the perfect fcc lattice: zero net force per site
+    and the per-site energy and virial of the crystallographic shells."""
+    st = inputs.lj_fluid(4 * 6 ** 3, 0.8442, 1.0, seed=1)
+    L = st.box[0, 0]
+    a = L / 6
+    f, vir, absf = oracle.pair_forces(pair, st.pos, L, r_cut, [c])
+    assert np.max(np.abs(f[:, :3])) <= 1e-12 * np.max(absf)
+    pe, w = 0.0, 0.0
+    for k, z in _fcc_shells():
+        r = a * math.sqrt(k / 2.0)
+        if r >= r_cut:
+            continue
+        fr, v = oracle.pair_eval(pair, r * r, c)
+        pe += 0.5 * z * v
+        w += 0.5 * z * fr * r * r
+    assert np.allclose(f[:, 3], pe, rtol=1e-12, atol=1e-13)
+    assert np.allclose(vir[:, 0] + vir[:, 3] + vir[:, 5], w, rtol=1e-11, atol=1e-12)
+
+
+def test_pair_forces_lj_kind_equals_lj_forces_and_rows_equal_brute():
+    """The generic pair sums with the LJ kind equal the LJ functions bit for
+    bit, and the row-driven sums equal the brute-force ones for a new kind."""
+    st = inputs.lj_fluid(864, 0.8442, 1.0, seed=4, jitter=0.1)
+    L = st.box[0, 0]
+    f1, v1, a1 = oracle.lj_forces(st.pos, L, 2.5)
+    f2, v2, a2 = oracle.pair_forces("lj", st.pos, L, 2.5, [[1.0, 1.0]])
+    assert np.array_equal(f1, f2) and np.array_equal(v1, v2)
+    nl = oracle.neighbors(st.pos, L, 2.8, max_nb=128)
+    fb, _, absf = oracle.pair_forces("yukawa", st.pos, L, 2.5, [[1.0, 1.0]])
+    fn, _, _ = oracle.pair_forces("yukawa", st.pos, L, 2.5, [[1.0, 1.0]], nlist=nl)
+    assert np.max(np.abs(fb[:, :3] - fn[:, :3])) <= 1e-13 * np.max(absf)
+
+
 def test_lj_multitype_coefficients_index_by_type_pair():
     st = inputs.lj_fluid(256, 0.8, 1.0, seed=4, jitter=0.1)
     L = st.box[0, 0]
