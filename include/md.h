@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 3
+#define MD_ABI_VERSION 4
 
 typedef struct md_system md_system;
 typedef struct CUstream_st *md_stream; /* a cudaStream_t; NULL = legacy default stream */
@@ -60,7 +60,20 @@ typedef enum {
 } md_status;
 
 typedef enum { MD_FP64 = 0, MD_MIXED = 1 } md_precision;
-typedef enum { MD_PAIR_LJ = 0, MD_PAIR_DPD = 1 } md_pair_kind;
+/* Pair potentials (Sec. 3 lists LJ, DPD, Gaussian, Morse and Yukawa among
+ * the supported pairs; textbook forms, force truncated at r_cut):
+ *   MD_PAIR_LJ      (eps, sigma):       V = 4 eps [(sigma/r)^12 - (sigma/r)^6]
+ *   MD_PAIR_DPD     (A, gamma):         Groot-Warren, see md_params.kT / seed
+ *   MD_PAIR_GAUSS   (eps, sigma):       V = eps exp(-r^2 / (2 sigma^2))
+ *   MD_PAIR_MORSE   (D0, alpha, r0):    V = D0 [e^(-2 alpha (r - r0)) - 2 e^(-alpha (r - r0))]
+ *   MD_PAIR_YUKAWA  (eps, kappa):       V = eps e^(-kappa r) / r */
+typedef enum {
+    MD_PAIR_LJ = 0,
+    MD_PAIR_DPD = 1,
+    MD_PAIR_GAUSS = 2,
+    MD_PAIR_MORSE = 3,
+    MD_PAIR_YUKAWA = 4
+} md_pair_kind;
 typedef enum { MD_KERNEL_NLIST = 0, MD_KERNEL_PAIR = 1 } md_kernel;
 typedef enum { MD_NVE = 0, MD_LANGEVIN = 1, MD_NOSE_HOOVER = 2 } md_integrator;
 
@@ -91,10 +104,12 @@ typedef struct {
     uint64_t seed;                 /* DPD noise key */
     int32_t pair;                  /* md_pair_kind */
     int32_t n_types;               /* >= 1, <= 32 */
-    const double *pair_coeff;      /* host [n_types][n_types][2]:
-                                      LJ (epsilon, sigma); DPD (A, gamma) */
+    const double *pair_coeff;      /* host [n_types][n_types][k], k = 3 for
+                                      Morse, else 2 (coefficients of
+                                      md_pair_kind, in its order); finite */
     int32_t precision;             /* md_precision */
-    int32_t shift_energy;          /* LJ: report V(r) - V(r_cut) as energy */
+    int32_t shift_energy;          /* LJ, Gaussian, Morse, Yukawa: report
+                                      V(r) - V(r_cut) as energy */
     int32_t max_nb;                /* neighbour row capacity (rounded up to 32) */
     int32_t sort_period;           /* sort at the first rebuild >= this many
                                       steps after the last sort; 0 = never */

@@ -101,6 +101,9 @@ struct Plan {
   size_t total = 0;
 };
 
+// Coefficients per ordered type pair of each pair kind (md.h).
+int pair_ncoeff(int32_t pair) { return pair == MD_PAIR_MORSE ? 3 : 2; }
+
 md_status validate(const md_params *p) {
   if (!p) return MD_ERR_INVALID_ARG;
   if (p->n_total < 0 || p->n_total > kMaxParticles) return MD_ERR_INVALID_ARG;
@@ -113,10 +116,12 @@ md_status validate(const md_params *p) {
     return MD_ERR_INVALID_ARG;
   if (!std::isfinite(p->r_cut) || !std::isfinite(p->r_skin) || !std::isfinite(p->dt))
     return MD_ERR_INVALID_ARG;
-  if (p->pair != MD_PAIR_LJ && p->pair != MD_PAIR_DPD) return MD_ERR_INVALID_ARG;
+  if (p->pair < MD_PAIR_LJ || p->pair > MD_PAIR_YUKAWA) return MD_ERR_INVALID_ARG;
   if (p->precision != MD_FP64 && p->precision != MD_MIXED) return MD_ERR_INVALID_ARG;
   if (p->n_types < 1 || p->n_types > kMaxTypes || !p->pair_coeff) return MD_ERR_INVALID_ARG;
   if (p->pair == MD_PAIR_DPD && !(p->kT >= 0)) return MD_ERR_INVALID_ARG;
+  for (int k = 0; k < pair_ncoeff(p->pair) * p->n_types * p->n_types; k++)
+    if (!std::isfinite(p->pair_coeff[k])) return MD_ERR_INVALID_ARG;
   if (p->max_nb < 1 || p->max_nb > (1 << 20)) return MD_ERR_INVALID_ARG;
   if (p->sort_period < 0 || p->thermo_period < 0 || p->graph_steps < 0 || p->max_bonds < 0)
     return MD_ERR_INVALID_ARG;
@@ -419,7 +424,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   const int R = p->n_replicas;
   s->off.assign(p->replica_offset, p->replica_offset + R + 1);
   s->box.assign(p->box, p->box + 3 * R);
-  s->coeff.assign(p->pair_coeff, p->pair_coeff + 2 * p->n_types * p->n_types);
+  s->coeff.assign(p->pair_coeff, p->pair_coeff + pair_ncoeff(p->pair) * p->n_types * p->n_types);
   s->p.replica_offset = s->off.data();
   s->p.box = s->box.data();
   s->p.pair_coeff = s->coeff.data();
@@ -574,8 +579,34 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   for (int ti = 0; ti < p->n_types; ti++)
     for (int tj = 0; tj < p->n_types; tj++) {
       const int c = ti * p->n_types + tj;
-      const double c0 = p->pair_coeff[2 * c], c1 = p->pair_coeff[2 * c + 1];
-      if (p->pair == MD_PAIR_LJ) {
+      const int nk = pair_ncoeff(p->pair);
+      const double c0 = p->pair_coeff[nk * c], c1 = p->pair_coeff[nk * c + 1];
+      if (p->pair == MD_PAIR_GAUSS || p->pair == MD_PAIR_MORSE || p->pair == MD_PAIR_YUKAWA) {
+        // Gaussian (eps, sigma), Morse (D0, alpha, r0), Yukawa (eps, kappa)
+        double k0 = 0, k1 = 0, k2 = 0, k3 = 0, vc = 0;
+        const double rc = p->r_cut;
+        if (p->pair == MD_PAIR_GAUSS) {
+          k0 = 1.0 / (2.0 * c1 * c1), k1 = c0 / (c1 * c1), k2 = c0;
+          vc = c0 * std::exp(-rc * rc * k0);
+        } else if (p->pair == MD_PAIR_MORSE) {
+          const double r0 = p->pair_coeff[nk * c + 2];
+          k0 = c1, k1 = r0, k2 = 2.0 * c0 * c1, k3 = c0;
+          const double x = std::exp(-c1 * (rc - r0));
+          vc = c0 * x * (x - 2.0);
+        } else {
+          k0 = c1, k1 = c0;
+          vc = c0 * std::exp(-c1 * rc) / rc;
+        }
+        if (!p->shift_energy) vc = 0.0;
+        if (mixed) {
+          PotCoeffF f{(float)k0, (float)k1, (float)k2, (float)k3, (float)vc, 0, 0, 0};
+          std::memcpy(coeff.data() + sizeof(PotCoeffF) * c, &f, sizeof(f));
+          if (c == 0) a.pot1f = f;
+        } else {
+          PotCoeffD d{k0, k1, k2, k3, vc, 0, 0, 0};
+          std::memcpy(coeff.data() + sizeof(PotCoeffD) * c, &d, sizeof(d));
+        }
+      } else if (p->pair == MD_PAIR_LJ) {
         const double eps = c0, sig = c1;
         const double s6 = std::pow(sig, 6), s12 = s6 * s6;
         const double sr6 = s6 / std::pow(p->r_cut, 6);

@@ -4,7 +4,7 @@
 
 namespace mdgb {
 
-constexpr int kLJ = 0, kDPD = 1;
+constexpr int kLJ = 0, kDPD = 1, kGauss = 2, kMorse = 3, kYukawa = 4;
 
 template <int POT, bool MIXED>
 cudaError_t launch_pair_form(const KArgs &a, Launch l, int want_virial, cudaStream_t st);
@@ -13,30 +13,53 @@ int max_block_pair_form(int w, int want_virial);
 template <int POT, bool MIXED>
 void pair_form_attributes();
 
+template <int POT>
+void form_attributes() {
+  pair_form_attributes<POT, true>();
+  pair_form_attributes<POT, false>();
+}
+
 void pair_init_attributes() {
-  pair_form_attributes<kLJ, true>();
-  pair_form_attributes<kLJ, false>();
-  pair_form_attributes<kDPD, true>();
-  pair_form_attributes<kDPD, false>();
+  form_attributes<kLJ>();
+  form_attributes<kDPD>();
+  form_attributes<kGauss>();
+  form_attributes<kMorse>();
+  form_attributes<kYukawa>();
+}
+
+template <int POT>
+cudaError_t launch_pot(const KArgs &a, Launch l, int want_virial, cudaStream_t st) {
+  return a.mixed ? launch_pair_form<POT, true>(a, l, want_virial, st)
+                 : launch_pair_form<POT, false>(a, l, want_virial, st);
 }
 
 cudaError_t launch_pair(const KArgs &a, Launch l, int want_virial, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  const bool m = a.mixed != 0;
-  if (a.pair == kLJ)
-    return m ? launch_pair_form<kLJ, true>(a, l, want_virial, st)
-             : launch_pair_form<kLJ, false>(a, l, want_virial, st);
-  return m ? launch_pair_form<kDPD, true>(a, l, want_virial, st)
-           : launch_pair_form<kDPD, false>(a, l, want_virial, st);
+  switch (a.pair) {
+    case kLJ: return launch_pot<kLJ>(a, l, want_virial, st);
+    case kDPD: return launch_pot<kDPD>(a, l, want_virial, st);
+    case kGauss: return launch_pot<kGauss>(a, l, want_virial, st);
+    case kMorse: return launch_pot<kMorse>(a, l, want_virial, st);
+    case kYukawa: return launch_pot<kYukawa>(a, l, want_virial, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int POT>
+int max_block_pot(const KArgs &a, int w, int want_virial) {
+  return a.mixed ? max_block_pair_form<POT, true>(w, want_virial)
+                 : max_block_pair_form<POT, false>(w, want_virial);
 }
 
 int max_block_pair(const KArgs &a, int w, int want_virial) {
-  const bool m = a.mixed != 0;
-  if (a.pair == kLJ)
-    return m ? max_block_pair_form<kLJ, true>(w, want_virial)
-             : max_block_pair_form<kLJ, false>(w, want_virial);
-  return m ? max_block_pair_form<kDPD, true>(w, want_virial)
-           : max_block_pair_form<kDPD, false>(w, want_virial);
+  switch (a.pair) {
+    case kLJ: return max_block_pot<kLJ>(a, w, want_virial);
+    case kDPD: return max_block_pot<kDPD>(a, w, want_virial);
+    case kGauss: return max_block_pot<kGauss>(a, w, want_virial);
+    case kMorse: return max_block_pot<kMorse>(a, w, want_virial);
+    case kYukawa: return max_block_pot<kYukawa>(a, w, want_virial);
+    default: return 0;
+  }
 }
 
 }  // namespace mdgb

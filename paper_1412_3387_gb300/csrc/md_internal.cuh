@@ -88,6 +88,11 @@ struct LJCoeffD { double lj1, lj2, lj3, lj4, vshift, pad0, pad1, pad2; };  // 64
 struct LJCoeffF { float lj1, lj2, lj3, lj4, vshift, pad0, pad1, pad2; };
 struct DPDCoeffD { double A, gamma, sigma_rdt, pad; };  // sigma / sqrt(dt)
 struct DPDCoeffF { float A, gamma, sigma_rdt, pad; };
+// Gaussian (c0 = 1 / (2 sigma^2), c1 = eps / sigma^2, c2 = eps), Morse
+// (c0 = alpha, c1 = r0, c2 = 2 D0 alpha, c3 = D0), Yukawa (c0 = kappa,
+// c1 = eps); vshift = V(r_cut) when energies are shifted.
+struct PotCoeffD { double c0, c1, c2, c3, vshift, pad0, pad1, pad2; };  // 64 B
+struct PotCoeffF { float c0, c1, c2, c3, vshift, pad0, pad1, pad2; };
 
 // Everything a kernel needs, passed by value (< 4 KB).
 struct KArgs {
@@ -142,12 +147,13 @@ struct KArgs {
   int4 *s_img;
   int32_t *s_tag, *s_type;
   float4 *s_oref;
-  const void *coeff;   // LJCoeff* / DPDCoeff* [ntypes^2], precision-matched
+  const void *coeff;   // LJCoeff* / DPDCoeff* / PotCoeff* [ntypes^2], precision-matched
   // the single type pair's FP32 coefficients, as kernel parameters: the
   // mixed pair loops take them as constant operands instead of re-loading
   // them from memory
   LJCoeffF lj1f;
   DPDCoeffF dpd1f;
+  PotCoeffF pot1f;
   // parameters
   int32_t max_nb;        // a multiple of 32
   int32_t w_store_log2;  // neighbour-list tile width (pair kernel's w)

@@ -8,9 +8,10 @@
 // each), so every neighbour position comes from shared memory and every
 // separation is a single FP32 subtraction per component.
 //
-// Potentials: LJ 12-6 (Sec. 3; benchmarks of Sec. 6, 8.3) and DPD in the
+// Potentials: LJ 12-6 (Sec. 3; benchmarks of Sec. 6, 8.3), DPD in the
 // Groot-Warren form with a Philox-4x32-10 pair noise keyed on the global IDs
-// (Sec. 9: per-pair generators seeded with global particle IDs).
+// (Sec. 9: per-pair generators seeded with global particle IDs), and the
+// Gaussian, Morse and Yukawa pairs of Sec. 3's list in their textbook forms.
 //
 // Precision forms:
 //   FP64  -- FP64 distance (fixed-order minimum image) and FP64 force math.
@@ -28,7 +29,7 @@
 
 namespace mdgb {
 
-constexpr int kLJ = 0, kDPD = 1;
+constexpr int kLJ = 0, kDPD = 1, kGauss = 2, kMorse = 3, kYukawa = 4;
 
 namespace {
 constexpr unsigned FULL = 0xffffffffu;
@@ -70,6 +71,48 @@ __device__ __forceinline__ double seg_sum(double v) {
   return v;
 }
 
+// Gaussian V = eps e^(-r^2 / 2 sigma^2), Morse V = D0 (x^2 - 2 x) with
+// x = e^(-alpha (r - r0)), Yukawa V = eps e^(-kappa r) / r: the force factor
+// fr = -dV/dr / r (f_ij = fr d_ij) at r^2, and V in v.  FP32 (mixed forms).
+template <int POT>
+__device__ __forceinline__ float pot_fr(const PotCoeffF &c, float r2, float &v) {
+  if (POT == kGauss) {
+    const float e = __expf(-c.c0 * r2);
+    v = c.c2 * e;
+    return c.c1 * e;
+  } else if (POT == kMorse) {
+    const float rinv = rsqrtf(r2), r = r2 * rinv;
+    const float x = __expf(-c.c0 * (r - c.c1));
+    v = c.c3 * x * (x - 2.f);
+    return c.c2 * x * (x - 1.f) * rinv;
+  } else {
+    const float rinv = rsqrtf(r2), r = r2 * rinv;
+    const float e = c.c1 * __expf(-c.c0 * r) * rinv;
+    v = e;
+    return e * fmaf(c.c0, r, 1.f) * rinv * rinv;
+  }
+}
+
+// The same in FP64.
+template <int POT>
+__device__ __forceinline__ double pot_fr(const PotCoeffD &c, double r2, double &v) {
+  if (POT == kGauss) {
+    const double e = exp(-c.c0 * r2);
+    v = c.c2 * e;
+    return c.c1 * e;
+  } else if (POT == kMorse) {
+    const double r = sqrt(r2);
+    const double x = exp(-c.c0 * (r - c.c1));
+    v = c.c3 * x * (x - 2.0);
+    return c.c2 * x * (x - 1.0) / r;
+  } else {
+    const double r = sqrt(r2);
+    const double e = c.c1 * exp(-c.c0 * r) / r;
+    v = e;
+    return e * (1.0 + c.c0 * r) / r2;
+  }
+}
+
 // Force on home particle i from the neighbour of entry e (mixed path).  Adds
 // to the group sums (gx, gy, gz) and, with ENERGY, to the energy and virial
 // Kahan sums.  Nothing happens beyond the cut-off.
@@ -86,6 +129,7 @@ struct MixedPair {
   float rc2_lo, rc2_hi, inv_rc;
   LJCoeffF lj0;
   DPDCoeffF dp0;
+  PotCoeffF pc0;
   __device__ __forceinline__ void operator()(uint32_t e, float &gx, float &gy, float &gz, KSum &kpe,
                                              KSum *kw) const {
     const float4 oj = src.pos(e);
@@ -104,6 +148,11 @@ struct MixedPair {
       const float r6 = r2i * r2i * r2i;
       fr = r2i * r6 * (c.lj1 * r6 - c.lj2);
       if (ENERGY) v = r6 * (c.lj3 * r6 - c.lj4) - c.vshift;
+    } else if (POT != kDPD) {
+      const PotCoeffF c = ONE ? pc0 : reinterpret_cast<const PotCoeffF *>(a.coeff)[cidx];
+      float vv;
+      fr = pot_fr<POT>(c, r2, vv);
+      if (ENERGY) v = vv - c.vshift;
     } else {
       const DPDCoeffF c = ONE ? dp0 : reinterpret_cast<const DPDCoeffF *>(a.coeff)[cidx];
       const float4 vj = src.vel(e);
@@ -143,6 +192,7 @@ struct DoublePair {
   float rc2_hi;
   LJCoeffD lj0;
   DPDCoeffD dp0;
+  PotCoeffD pd0;
   __device__ __forceinline__ void operator()(uint32_t e, double *df, double &dpe, double *dw) const {
     const float4 oj = src.pos(e);
     const float fx32 = oi.x - oj.x, fy32 = oi.y - oj.y, fz32 = oi.z - oj.z;
@@ -160,6 +210,11 @@ struct DoublePair {
       const double r6 = r2i * r2i * r2i;
       fr = r2i * r6 * (c.lj1 * r6 - c.lj2);
       if (ENERGY) v = r6 * (c.lj3 * r6 - c.lj4) - c.vshift;
+    } else if (POT != kDPD) {
+      const PotCoeffD c = ONE ? pd0 : reinterpret_cast<const PotCoeffD *>(a.coeff)[cidx];
+      double vv;
+      fr = pot_fr<POT>(c, r2d, vv);
+      if (ENERGY) v = vv - c.vshift;
     } else {
       const DPDCoeffD c = ONE ? dp0 : reinterpret_cast<const DPDCoeffD *>(a.coeff)[cidx];
       const double4 vj = ld_d4(a.vel + j);
@@ -268,7 +323,8 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
     mp.inv_rc = (float)(1.0 / a.r_cut);
     if (ONE) {
       if (POT == kLJ) mp.lj0 = a.lj1f;
-      else mp.dp0 = a.dpd1f;
+      else if (POT == kDPD) mp.dp0 = a.dpd1f;
+      else mp.pc0 = a.pot1f;
     }
     if (POT == kDPD) {
       mp.vi4 = src.vel((uint32_t)(hs.slot + 1));
@@ -283,7 +339,8 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
     dp.rc2_hi = a.rc2f + rp.band;
     if (ONE) {
       if (POT == kLJ) dp.lj0 = reinterpret_cast<const LJCoeffD *>(a.coeff)[0];
-      else dp.dp0 = reinterpret_cast<const DPDCoeffD *>(a.coeff)[0];
+      else if (POT == kDPD) dp.dp0 = reinterpret_cast<const DPDCoeffD *>(a.coeff)[0];
+      else dp.pd0 = reinterpret_cast<const PotCoeffD *>(a.coeff)[0];
     }
     if (POT == kDPD) {
       dp.vi = ld_d4(a.vel + i);
@@ -324,6 +381,7 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
   // memory load from the parameter buffer inside the loop.
   const LJCoeffF lj = a.lj1f;
   const DPDCoeffF dc = a.dpd1f;
+  const PotCoeffF pc = a.pot1f;
   const int ntypes = a.ntypes, ti = cell_type(__float_as_uint(oi.w));
   const void *coeff = a.coeff;
   const float inv_rc = (float)(1.0 / a.r_cut), r_cut_f = (float)a.r_cut;
@@ -351,6 +409,14 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
         const float r6 = r2i * r2i * r2i;
         fr = in ? r2i * r6 * (c.lj1 * r6 - c.lj2) : 0.f;
         if (ENERGY) en = in ? r6 * (c.lj3 * r6 - c.lj4) - c.vshift : 0.f;
+      } else if (POT != kDPD) {
+        const PotCoeffF c = ONE ? pc
+                                : reinterpret_cast<const PotCoeffF *>(coeff)[
+                                      ti * ntypes + cell_type(__float_as_uint(ojw))];
+        float vv;
+        const float f = pot_fr<POT>(c, r2, vv);
+        fr = in ? f : 0.f;
+        if (ENERGY) en = in ? vv - c.vshift : 0.f;
       } else {
         const DPDCoeffF c = ONE ? dc
                                 : reinterpret_cast<const DPDCoeffF *>(coeff)[

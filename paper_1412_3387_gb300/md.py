@@ -23,7 +23,10 @@ STATUS = {
     7: "MD_ERR_CELL_OVERFLOW", 8: "MD_ERR_STATE", 9: "MD_ERR_TIMEOUT",
 }
 FP64, MIXED = 0, 1
-LJ, DPD = 0, 1
+LJ, DPD, GAUSS, MORSE, YUKAWA = 0, 1, 2, 3, 4
+# pair kinds by name, and their coefficients per ordered type pair (md.h)
+PAIRS = {"lj": LJ, "dpd": DPD, "gauss": GAUSS, "morse": MORSE, "yukawa": YUKAWA}
+PAIR_NCOEFF = {LJ: 2, DPD: 2, GAUSS: 2, MORSE: 3, YUKAWA: 2}
 KERNEL_NLIST, KERNEL_PAIR = 0, 1
 THERMO_FIELDS = ("ke", "pe", "virial", "pressure", "temperature", "px", "py", "pz")
 
@@ -144,11 +147,16 @@ class MDSystem:
         self.image = t(state.image, torch.int32)
         self.tag = t(state.tag, torch.int32)
         self.type = t(state.type, torch.int32)
+        if pair not in PAIRS:
+            raise ValueError(f"unknown pair kind {pair!r}")
+        nk = PAIR_NCOEFF[PAIRS[pair]]
         coeff = np.ascontiguousarray(coeff, np.float64)
-        n_types = int(round(np.sqrt(coeff.size / 2)))
+        n_types = int(round(np.sqrt(coeff.size / nk)))
+        if n_types * n_types * nk != coeff.size:
+            raise ValueError(f"{pair} needs {nk} coefficients per ordered type pair")
         self._off = np.ascontiguousarray(state.offsets, np.int64)
         self._box = np.ascontiguousarray(state.box, np.float64).reshape(-1, 3)
-        self._coeff = coeff.reshape(n_types, n_types, 2).copy()
+        self._coeff = coeff.reshape(n_types, n_types, nk).copy()
         bonds = getattr(state, "bonds", None)
         if max_bonds is None:
             if bonds is not None and len(bonds):
@@ -165,7 +173,7 @@ class MDSystem:
         p.box = self._box.ctypes.data
         p.r_cut, p.r_skin, p.dt, p.mass, p.kT = r_cut, r_skin, dt, mass, kT
         p.seed = int(seed)
-        p.pair = LJ if pair == "lj" else DPD
+        p.pair = PAIRS[pair]
         p.n_types = n_types
         p.pair_coeff = self._coeff.ctypes.data
         p.precision = FP64 if precision == "fp64" else MIXED
