@@ -14,7 +14,8 @@ Metric: particle-timesteps/s (N * steps / wall), higher is better; TPS is
 reported beside it.  Also reported ("forms"): the plain FP64 path on the same
 state; the 256-replica ensemble (mixed) and the same replicas as 256
 sequential FP64 runs; the 4,000-particle FP64 fluid; the 8,000,000-particle
-DPD fluid; the 4,194,304-bead diblock melt (mixed and FP64); each form's force
+DPD fluid; the 4,194,304-bead diblock melt (mixed and FP64); the Gaussian,
+Morse and Yukawa pairs on the 2,097,152-particle fluid (mixed); each form's force
 error against the CPU oracle; the pair kernels' rooflines; the CPU oracle on
 bounded samples (all host threads and one thread); an end-to-end figure with
 host buffers.
@@ -486,6 +487,35 @@ def small_fp64_form(md, dev, stream, torch):
             "steps": 100, "graph_steps_used": 100, "n_particles": 4000}
 
 
+# Gaussian, Morse and Yukawa pairs (Sec. 3's list): the paper's 2,097,152-
+# particle benchmark fluid (rho 0.8442, T 1.2) with each potential in the
+# mixed form, 100 untimed steps from the lattice, then timed graph replays
+POTENTIALS = (("gauss", [[1.0, 1.0]]), ("morse", [[1.0, 2.0, 1.1]]), ("yukawa", [[1.0, 1.0]]))
+
+
+def potential_forms(md, dev, stream, torch, tune_used, n=2_097_152, steps=200):
+    out = {}
+    for name, coeff in POTENTIALS:
+        st = inputs.lj_fluid(n, 0.8442, 1.2, seed=2727)
+        g = graph_len(steps)
+        s = md.MDSystem(st, r_cut=2.5, r_skin=0.4, dt=0.005, pair=name, coeff=coeff,
+                        precision="mixed", sort_period=1, thermo_period=g, graph_steps=g,
+                        stream=stream)
+        for kern, k in ((md.KERNEL_PAIR, "pair"), (md.KERNEL_NLIST, "nlist")):
+            s.set_tuning(kern, *tune_used[k])
+        s.run(100, stream=stream)
+        ready_for_graphs(s, g, stream, torch)
+        t = time_run(s, steps, stream, torch)
+        s.check_error()
+        out[name] = {"value": n * steps / t, "ms_per_step": 1e3 * t / steps, "steps": steps,
+                     "graph_steps_used": g, "n_particles": n, "coeff": coeff,
+                     "pair_ms_per_launch": pair_launch_ms(s, stream, torch, 10)}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return {"potentials_2M_mixed": out}
+
+
 def dpd_forms(md, dev, stream, torch, args):
     """DPD fluid (8,000,000, rho 3, A 25, gamma 4.5, kT 1, dt 0.02, mixed) and
     the diblock melt (131,072 chains x 32 beads, A_AB 40, K 4), each with its
@@ -746,6 +776,8 @@ def main():
             forms["lj4000_fp64"] = small_fp64_form(md, dev, stream, torch)
         if want("dpd"):
             forms.update(dpd_forms(md, dev, stream, torch, args))
+        if want("potentials"):
+            forms.update(potential_forms(md, dev, stream, torch, tune_used))
 
     if rank != 0:
         return
