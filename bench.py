@@ -490,7 +490,7 @@ def small_fp64_form(md, dev, stream, torch):
 # Gaussian, Morse and Yukawa pairs (Sec. 3's list): the paper's 2,097,152-
 # particle benchmark fluid (rho 0.8442, T 1.2) with each potential in the
 # mixed form, 100 untimed steps from the lattice, then timed graph replays
-POTENTIALS = (("gauss", [[1.0, 1.0]]), ("morse", [[1.0, 2.0, 1.1]]), ("yukawa", [[1.0, 1.0]]))
+POTENTIALS = (("gauss", [[1.0, 1.0]]), ("morse", [[1.0, 6.0, 1.12]]), ("yukawa", [[1.0, 1.0]]))
 
 
 def potential_forms(md, dev, stream, torch, tune_used, n=2_097_152, steps=200):
@@ -500,16 +500,19 @@ def potential_forms(md, dev, stream, torch, tune_used, n=2_097_152, steps=200):
         g = graph_len(steps)
         s = md.MDSystem(st, r_cut=2.5, r_skin=0.4, dt=0.005, pair=name, coeff=coeff,
                         precision="mixed", sort_period=1, thermo_period=g, graph_steps=g,
-                        stream=stream)
-        for kern, k in ((md.KERNEL_PAIR, "pair"), (md.KERNEL_NLIST, "nlist")):
-            s.set_tuning(kern, *tune_used[k])
-        s.run(100, stream=stream)
-        ready_for_graphs(s, g, stream, torch)
-        t = time_run(s, steps, stream, torch)
-        s.check_error()
-        out[name] = {"value": n * steps / t, "ms_per_step": 1e3 * t / steps, "steps": steps,
-                     "graph_steps_used": g, "n_particles": n, "coeff": coeff,
-                     "pair_ms_per_launch": pair_launch_ms(s, stream, torch, 10)}
+                        max_nb=192, stream=stream)
+        try:
+            for kern, k in ((md.KERNEL_PAIR, "pair"), (md.KERNEL_NLIST, "nlist")):
+                s.set_tuning(kern, *tune_used[k])
+            s.run(100, stream=stream)
+            ready_for_graphs(s, g, stream, torch)
+            t = time_run(s, steps, stream, torch)
+            s.check_error()
+            out[name] = {"value": n * steps / t, "ms_per_step": 1e3 * t / steps, "steps": steps,
+                         "graph_steps_used": g, "n_particles": n, "coeff": coeff,
+                         "pair_ms_per_launch": pair_launch_ms(s, stream, torch, 10)}
+        except md.MDError as e:  # a side leg never hides the headline
+            out[name] = {"error": str(e), "coeff": coeff}
         s.close()
         del s
         torch.cuda.empty_cache()
