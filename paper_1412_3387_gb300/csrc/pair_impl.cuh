@@ -307,18 +307,6 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
   const int bstride = (FULLG ? 32 : pj * W) * V;    // entries per block
   const uint16_t *row = a.nl + (size_t)pg * (size_t)a.max_nb + (qe * W + sl) * V;
   auto ldrow = [&](int b) { return b < NB ? RW::load(row + (size_t)b * bstride) : RW::zero(); };
-  {
-    // the first blocks of this warp's next group of the brick, into L1 now:
-    // that group then starts on cache hits instead of a trip to L2
-    const int jn = j + (int)(blockDim.x >> 5);
-    if (jn * P < d.nhome) {
-      const int pn = min(P, d.nhome - jn * P);
-      const uint16_t *rn = a.nl + (size_t)(d.hstart + jn * P) * (size_t)a.max_nb +
-                           ((qq < pn ? qq : 0) * W + sl) * V;
-#pragma unroll
-      for (int k = 0; k < 4; k++) prefetch_l1(rn + (size_t)k * (size_t)(pn * W * V));
-    }
-  }
 
   KSum kf[3], kpe, kw[6];
   double df[3] = {0., 0., 0.}, dpe = 0., dw[6] = {0., 0., 0., 0., 0., 0.};
