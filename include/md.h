@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 4
+#define MD_ABI_VERSION 5
 
 typedef struct md_system md_system;
 typedef struct CUstream_st *md_stream; /* a cudaStream_t; NULL = legacy default stream */
@@ -261,6 +261,19 @@ md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream st
  * first half step from the velocities at that time (call this again after
  * writing velocities directly).  Not valid with DPD pair forces (their
  * noise and friction are the thermostat).  Errors: MD_ERR_INVALID_ARG. */
+/* Half neighbour list with Newton's third law, FP64 forms only (Sec. 5.1
+ * discusses full lists; the survey's "half list" row): with enable = 1 each
+ * pair within r_list is listed once, in the row of the particle with the
+ * smaller cell-list position, and the pair kernel evaluates it once, adding
+ * f_ij to that particle and -f_ij (and half the pair energy and virial) to
+ * the partner with FP64 atomic adds.  Halves the FP64 pair arithmetic, the
+ * bound of the FP64 form.  The order of the atomic adds varies from run to
+ * run, so FP64 forces are reproducible only to rounding (within the 1e-12
+ * rule), not bit for bit; md_get_nlist then returns the half rows.  The
+ * list is rebuilt at the next step.  Errors: MD_ERR_INVALID_ARG (enable not
+ * 0 or 1, or a mixed-precision system). */
+md_status md_set_newton(md_system *s, int32_t enable);
+
 md_status md_set_integrator(md_system *s, int32_t kind, double kT, double param,
                             uint64_t seed);
 

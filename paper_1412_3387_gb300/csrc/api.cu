@@ -854,6 +854,17 @@ md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream st
   return MD_OK;
 }
 
+md_status md_set_newton(md_system *s, int32_t enable) {
+  if (!s || (enable != 0 && enable != 1)) return MD_ERR_INVALID_ARG;
+  if (enable && s->p.precision != MD_FP64) return MD_ERR_INVALID_ARG;
+  if (s->a.half != enable) {
+    s->a.half = enable;
+    s->built = s->listed = false;  // rows must be rebuilt in the new form
+    s->gvalid = false;
+  }
+  return MD_OK;
+}
+
 md_status md_set_integrator(md_system *s, int32_t kind, double kT, double param, uint64_t seed) {
   if (!s) return MD_ERR_INVALID_ARG;
   if (kind != MD_NVE && kind != MD_LANGEVIN && kind != MD_NOSE_HOOVER) return MD_ERR_INVALID_ARG;

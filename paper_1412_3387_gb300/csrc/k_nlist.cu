@@ -19,6 +19,10 @@
 // block; within a block, lane by lane, each lane's hits in slot order) with
 // no scratch storage.
 //
+// Half lists (md_set_newton): a pair is kept only in the row of the particle
+// with the smaller cell-list position, and the FP64 pair kernel applies
+// Newton's third law.
+//
 // Distance test.  Candidates are screened in FP32; a candidate whose FP32 r^2
 // lies within a proven error band of r_list^2 is re-tested with the FP64
 // minimum-image distance in the oracle's operation order.  The neighbour sets
@@ -90,6 +94,10 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
   for (int rr = 0; rr < 9; rr++) {
     const int s = c0 + 4 * (rr % 3) + 16 * (rr / 3);
     int rlo = d.off[s], len = d.off[s + 3] - rlo;
+    // cell-list position of a slot of this run (half lists): start of its
+    // stage cell (s, s + 1 or s + 2) plus its place in the cell
+    const int o1 = d.off[s + 1], o2 = d.off[s + 2];
+    const int b0 = d.start[s] - d.off[s], b1 = d.start[s + 1] - o1, b2 = d.start[s + 2] - o2;
     if (!DIRECT) {
       const int dyi = rr % 3, dzi = rr / 3;
       const float ry = fmaxf((dyi == 0 ? yb : dyi == 2 ? hy - yb : 0.f) - eps, 0.f);
@@ -186,6 +194,18 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
         m &= (1u << min(max(mylen - x0, 0), U)) - 1u;
         const int so = hs.slot - (beg + x0);
         if ((unsigned)so < (unsigned)U) m &= ~(1u << so);
+      }
+      if (a.half) {
+        // half list: a pair stays only in the row of the particle with the
+        // smaller cell-list position
+        unsigned keep = 0u;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int slot = beg + x0 + u;
+          const int g = slot + (slot < o1 ? b0 : slot < o2 ? b1 : b2);
+          keep |= (g > p ? 1u : 0u) << u;
+        }
+        m &= keep;
       }
       // compact: this lane's hits follow those of the particle's lower lanes
       const int h = __popc(m);

@@ -35,6 +35,13 @@ cudaError_t launch_pot(const KArgs &a, Launch l, int want_virial, cudaStream_t s
 
 cudaError_t launch_pair(const KArgs &a, Launch l, int want_virial, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
+  if (a.half && !a.mixed) {
+    // half list: both particles of a pair add into their sums
+    cudaError_t e = cudaMemsetAsync(a.force, 0, sizeof(double) * 4 * (size_t)a.n, st);
+    if (e == cudaSuccess && want_virial)
+      e = cudaMemsetAsync(a.virial, 0, sizeof(double) * 6 * (size_t)a.n, st);
+    if (e != cudaSuccess) return e;
+  }
   switch (a.pair) {
     case kLJ: return launch_pot<kLJ>(a, l, want_virial, st);
     case kDPD: return launch_pot<kDPD>(a, l, want_virial, st);

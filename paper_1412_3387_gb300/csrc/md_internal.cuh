@@ -161,6 +161,10 @@ struct KArgs {
   int32_t max_bonds;
   int32_t mixed;
   int32_t pair;
+  // half list (md_set_newton): each pair's row entry only in the row of the
+  // particle with the smaller cell-list position; the FP64 pair kernel adds
+  // -f_ij to the partner with atomics
+  int32_t half;
   double r_cut, rc2, rl2;
   float rc2f, rl2f;
   double dt, mass, kT;

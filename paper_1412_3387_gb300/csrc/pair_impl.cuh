@@ -193,6 +193,7 @@ struct DoublePair {
   LJCoeffD lj0;
   DPDCoeffD dp0;
   PotCoeffD pd0;
+  bool half;  // half list: the partner receives -f_ij here
   __device__ __forceinline__ void operator()(uint32_t e, double *df, double &dpe, double *dw) const {
     const float4 oj = src.pos(e);
     const float fx32 = oi.x - oj.x, fy32 = oi.y - oj.y, fz32 = oi.z - oj.z;
@@ -235,6 +236,21 @@ struct DoublePair {
       dpe += 0.5 * v;
       dw[0] += 0.5 * d[0] * fx; dw[1] += 0.5 * d[0] * fy; dw[2] += 0.5 * d[0] * fz;
       dw[3] += 0.5 * d[1] * fy; dw[4] += 0.5 * d[1] * fz; dw[5] += 0.5 * d[2] * fz;
+    }
+    if (half) {
+      // Newton's third law: -f_ij on the partner, and the other half of the
+      // pair's energy and virial (d and f both change sign)
+      double *fj = reinterpret_cast<double *>(a.force) + 4 * (int64_t)j;
+      atomicAdd(fj + 0, -fx);
+      atomicAdd(fj + 1, -fy);
+      atomicAdd(fj + 2, -fz);
+      if (ENERGY) {
+        atomicAdd(fj + 3, 0.5 * v);
+        double *wj = reinterpret_cast<double *>(a.virial) + 6 * (int64_t)j;
+        atomicAdd(wj + 0, 0.5 * d[0] * fx); atomicAdd(wj + 1, 0.5 * d[0] * fy);
+        atomicAdd(wj + 2, 0.5 * d[0] * fz); atomicAdd(wj + 3, 0.5 * d[1] * fy);
+        atomicAdd(wj + 4, 0.5 * d[1] * fz); atomicAdd(wj + 5, 0.5 * d[2] * fz);
+      }
     }
   }
 };
@@ -332,6 +348,7 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
     }
   } else {
     dp.oi = oi;
+    dp.half = a.half != 0;
     dp.ti = cell_type(__float_as_uint(oi.w));
     dp.ident = ident;
     dp.pi = ld_d4(a.pos + i);
@@ -525,7 +542,19 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
 #pragma unroll
       for (int c = 0; c < 6; c++) dw[c] = seg_sum<W>(dw[c]);
     }
-    if (active && sl == 0) {
+    if (active && sl == 0 && dp.half) {
+      // half list: partners add into this particle concurrently
+      double *f = reinterpret_cast<double *>(a.force) + 4 * (int64_t)i;
+      atomicAdd(f + 0, df[0]);
+      atomicAdd(f + 1, df[1]);
+      atomicAdd(f + 2, df[2]);
+      if (ENERGY) {
+        atomicAdd(f + 3, dpe);
+        double *vv = reinterpret_cast<double *>(a.virial) + 6 * (int64_t)i;
+#pragma unroll
+        for (int c = 0; c < 6; c++) atomicAdd(vv + c, dw[c]);
+      }
+    } else if (active && sl == 0) {
       double2 *f = reinterpret_cast<double2 *>(reinterpret_cast<double4 *>(a.force) + i);
       f[0] = make_double2(df[0], df[1]);
       f[1] = make_double2(df[2], ENERGY ? dpe : 0.);
@@ -588,12 +617,19 @@ __global__ void __launch_bounds__(kMaxBrickThreads) k_pair(KArgs a, int cap) {
     const bool has1 = bt + G < a.n_bricks, has2 = bt + 2 * G < a.n_bricks;
     if (has1) {
       stage_issue(a, M.desc(t + 1), M.pos(t + 1), VEL ? M.vel4(t + 1) : nullptr, M.bar(t + 1), cap);
-      // the next brick's row region (its particles' reserved rows, a
-      // multiple of 64 bytes) into L2 while this brick is computed
-      if (threadIdx.x == (blockDim.x > 32 ? 32 : 0)) {
+      // the next brick's rows into L2 while this brick is computed: per row
+      // group, the tiles its list build wrote (a group's tiles are one
+      // contiguous run from its base; 16-byte multiples, 64-byte aligned)
+      const int lane0 = blockDim.x > 32 ? 32 : 0;
+      if ((int)threadIdx.x >= lane0 && (int)threadIdx.x < lane0 + 32) {
         const BrickDesc &dn = M.desc(t + 1);
-        prefetch_l2(a.nl + (size_t)dn.hstart * (size_t)a.max_nb,
-                    (uint32_t)((size_t)dn.nhome * (size_t)a.max_nb * sizeof(uint16_t)));
+        const int gn = (dn.nhome + P - 1) / P;
+        for (int g = (int)threadIdx.x - lane0; g < gn; g += 32) {
+          const int pg = dn.hstart + g * P;
+          const uint32_t bytes = (uint32_t)__ldg(a.nl_tiles + pg) *
+                                 (uint32_t)(min(P, dn.nhome - g * P) * W) * 2u;
+          if (bytes > 0u) prefetch_l2(a.nl + (size_t)pg * (size_t)a.max_nb, (bytes + 15u) & ~15u);
+        }
       }
     }
     // the descriptor two bricks ahead: loaded now, stored after the work

@@ -79,6 +79,7 @@ SIGNATURES = {
     "md_philox4x32_10": (C.c_int, [_P, _P, _I64, _P]),
     "md_lj_forces_noalloc": (C.c_int, [_P, _I64, _P, _D, _D, _D, _P, _P]),
     "md_set_integrator": (C.c_int, [_P, _I32, _D, _D, C.c_uint64]),
+    "md_set_newton": (C.c_int, [_P, _I32]),
     "md_get_thermostat": (C.c_int, [_P, _P]),
 }
 INTEGRATORS = {"nve": 0, "langevin": 1, "nose-hoover": 2}
@@ -269,6 +270,11 @@ class MDSystem:
         check(self.lib.md_reduce_thermo(self.handle, _ptr(out), _stream(stream)),
               "md_reduce_thermo")
         return out
+
+    def set_newton(self, enable=True):
+        """Half neighbour list with Newton's third law (FP64 systems); see
+        md_set_newton."""
+        check(self.lib.md_set_newton(self.handle, int(bool(enable))), "md_set_newton")
 
     def set_integrator(self, kind="nve", kT=1.0, param=1.0, seed=0):
         """kind: "nve", "langevin" (param = friction gamma) or "nose-hoover"
