@@ -746,6 +746,16 @@ def main():
                                                "peak_source": "measured (DFMA chains, this run)",
                                                "fp64_instructions_per_pair": 40.0,
                                                "pairs_per_particle": 55.3}}
+            # the same FP64 run with the half list (Newton's third law): each
+            # pair's FP64 arithmetic once, the partner's share by atomic adds
+            s64.set_newton(True)
+            ready_for_graphs(s64, g64, stream, torch)
+            tn64 = time_run(s64, args.fp64_steps, stream, torch)
+            s64.check_error()
+            forms["fp64_newton"] = {"value": args.n * args.fp64_steps / tn64,
+                                    "ms_per_step": 1e3 * tn64 / args.fp64_steps,
+                                    "steps": args.fp64_steps, "graph_steps_used": g64,
+                                    "pair_ms_per_launch": pair_launch_ms(s64, stream, torch, 5)}
             s64.close()
             del s64
             torch.cuda.empty_cache()

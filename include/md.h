@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 5
+#define MD_ABI_VERSION 6
 
 typedef struct md_system md_system;
 typedef struct CUstream_st *md_stream; /* a cudaStream_t; NULL = legacy default stream */
@@ -54,10 +54,15 @@ typedef enum {
                                         one the periodic wrap cannot bring into the box */
     MD_ERR_CELL_OVERFLOW = 7,        /* a cell held more particles than can be ordered */
     MD_ERR_STATE = 8,                /* call not valid in the current state */
-    MD_ERR_TIMEOUT = 9               /* a kernel's wait for its own shared-memory copies gave
+    MD_ERR_TIMEOUT = 9,              /* a kernel's wait for its own shared-memory copies gave
                                         up after about a second (an internal error); the
                                         kernel returned early */
+    MD_ERR_BOND = 10                 /* a FENE bond reached its maximum extension R0;
+                                        detail = the particle index */
 } md_status;
+
+/* Bond styles (Sec. 3 lists harmonic and FENE bonds). */
+typedef enum { MD_BOND_HARMONIC = 0, MD_BOND_FENE = 1 } md_bond_style;
 
 typedef enum { MD_FP64 = 0, MD_MIXED = 1 } md_precision;
 /* Pair potentials (Sec. 3 lists LJ, DPD, Gaussian, Morse and Yukawa among
@@ -159,6 +164,16 @@ md_status md_destroy_system(md_system *s);
  * max_bonds partners.  Synchronises `stream`. */
 md_status md_set_bonds(md_system *s, const int32_t *bond_tags, int64_t n_bonds,
                        double K, double r0, md_stream stream);
+
+/* Bond style of md_set_bonds' bonds (Sec. 3 lists harmonic and FENE bonds):
+ *   MD_BOND_HARMONIC  V = K/2 (r - r0)^2 (the default)
+ *   MD_BOND_FENE      V = -K R0^2 / 2 ln(1 - (r / R0)^2), R0 = the r0 given to
+ *                     md_set_bonds (> 0); finitely extensible, no repulsive
+ *                     core (add it through the pair potential).  A bond at
+ *                     r >= R0 contributes nothing and raises MD_ERR_BOND in the
+ *                     device error word.
+ * Errors: MD_ERR_INVALID_ARG (unknown style; FENE with r0 <= 0). */
+md_status md_set_bond_style(md_system *s, int32_t style);
 
 /* Space-filling-curve sort (Sec. 4.3.1: the particle arrays, positions,
  * velocities and the rest, are reordered together, infrequently, at list
@@ -310,7 +325,8 @@ md_status md_get_step(md_system *s, int64_t *step); /* synchronises */
  * recorded error, in this order of precedence: MD_ERR_NLIST_OVERFLOW
  * (*detail = the max_nb needed), MD_ERR_NONFINITE (*detail = the index of a
  * particle with a non-finite position, or a finite one more than 1e9 box
- * lengths outside the box), MD_ERR_CELL_OVERFLOW, MD_ERR_STATE (a
+ * lengths outside the box), MD_ERR_BOND (*detail = the index of a particle
+ * with a FENE bond at or beyond R0), MD_ERR_CELL_OVERFLOW, MD_ERR_STATE (a
  * force evaluation found its replica's list stale and computed nothing),
  * MD_ERR_TIMEOUT.  The word is not cleared.  detail may be NULL. */
 md_status md_poll_error(md_system *s, int64_t *detail);

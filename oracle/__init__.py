@@ -50,7 +50,7 @@ class Params(C.Structure):
         ("n_bonds", C.c_int64), ("bonds", C.c_void_p), ("step0", C.c_int64),
         ("max_nb", C.c_int32), ("integrator", C.c_int32), ("t_kT", C.c_double),
         ("t_gamma", C.c_double), ("t_tau", C.c_double), ("t_seed", C.c_uint64),
-        ("nh_state", C.c_void_p),
+        ("nh_state", C.c_void_p), ("bond_style", C.c_int32),
     ]
 
 
@@ -79,6 +79,7 @@ def lib():
                 "orc_dpd_forces_brute": (None, [I64, P, P, P, P, P, D, I32, P, D, D, U64, U64, P, P, P]),
                 "orc_dpd_forces_nlist": (None, [I64, P, P, P, P, P, D, I32, P, D, D, U64, U64, P, P, I32, P, P, P]),
                 "orc_bond_forces": (None, [I64, P, P, P, D, D, P, P, P]),
+                "orc_fene_bond_forces": (I64, [I64, P, P, P, D, D, P, P, P]),
                 "orc_vv_first": (None, [I64, P, P, P, P, D, D, P]),
                 "orc_vv_second": (None, [I64, P, P, D, D]),
                 "orc_thermo": (None, [I64, P, P, P, D, P, P]),
@@ -269,6 +270,20 @@ def bond_forces(bonds, pos, L, K, r0, force=None, virial=None, absf=None):
     return force, virial, absf
 
 
+def fene_bond_forces(bonds, pos, L, K, R0, force=None, virial=None, absf=None):
+    """Adds FENE-bond forces to (force, virial, absf); returns them and the
+    number of bonds stretched to R0 or beyond (skipped)."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    bonds = _i32(bonds).reshape(-1, 2)
+    force = np.zeros((n, 4)) if force is None else _f64(force).copy()
+    virial = np.zeros((n, 6)) if virial is None else _f64(virial).copy()
+    absf = np.zeros(n) if absf is None else _f64(absf).copy()
+    broken = lib().orc_fene_bond_forces(bonds.shape[0], _p(bonds), _p(pos), _p(_box(L)),
+                                        float(K), float(R0), _p(force), _p(virial), _p(absf))
+    return force, virial, absf, int(broken)
+
+
 def vv_first(pos, vel, image, force, dt, L, mass=1.0):
     pos, vel, force = _f64(pos).copy(), _f64(vel).copy(), _f64(force)
     image = _i32(image).copy()
@@ -338,7 +353,8 @@ INTEGRATORS = {"nve": 0, "langevin": 1, "nose-hoover": 2}
 def run(pos, vel, image, L, n_steps, *, r_cut, r_skin, dt, pair="lj", type=None,
         tag=None, coeff=((1.0, 1.0),), kT=1.0, seed=0, mass=1.0, shift_energy=False,
         thermo_period=0, bonds=None, K=0.0, r0=0.0, step0=0, max_nb=256,
-        integrator="nve", t_kT=1.0, gamma=1.0, tau=1.0, t_seed=0, nh_state=None):
+        integrator="nve", t_kT=1.0, gamma=1.0, tau=1.0, t_seed=0, nh_state=None,
+        bond_style="harmonic"):
     """Full MD loop on copies of the inputs; returns a dict with the final
     state, forces, thermo rows, the number of list builds and (Nose-Hoover)
     the thermostat state [xi, eta] (nh_state gives its initial value)."""
@@ -370,6 +386,7 @@ def run(pos, vel, image, L, n_steps, *, r_cut, r_skin, dt, pair="lj", type=None,
     p.t_kT, p.t_gamma, p.t_tau, p.t_seed = float(t_kT), float(gamma), float(tau), int(t_seed)
     nh = np.ascontiguousarray(np.zeros(2) if nh_state is None else nh_state, np.float64).copy()
     p.nh_state = nh.ctypes.data
+    p.bond_style = {"harmonic": 0, "fene": 1}[bond_style]
     n_th = (n_steps // thermo_period + 1) if thermo_period else 0
     th = np.zeros((max(n_th, 1), 8))
     builds = lib().orc_run(n, _p(pos), _p(vel), _p(image), _p(t), _p(g), _p(force),

@@ -470,6 +470,49 @@ void orc_dpd_forces_nlist(int64_t n, const double *pos, const double *vel,
  * unordered pair of particle IDs): V = K/2 (r - r0)^2,
  * F_i = -K (r - r0) (x_i - x_j) / r, and F_j = -F_i.                        */
 
+/* FENE bond (Sec. 3 lists FENE bonds; the finitely extensible nonlinear
+ * elastic spring of Kremer and Grest, without the repulsive core):
+ * V = -K R0^2 / 2 ln(1 - (r / R0)^2), -dV/dr = -K r / (1 - (r / R0)^2).
+ * Returns the number of bonds at r >= R0 (undefined; skipped). */
+int64_t orc_fene_bond_forces(int64_t n_bonds, const int32_t *bonds, const double *pos,
+                             const double *L, double K, double R0, double *force,
+                             double *virial, double *absf) {
+    int64_t broken = 0;
+    for (int64_t b = 0; b < n_bonds; b++) {
+        int64_t i = bonds[2 * b], j = bonds[2 * b + 1];
+        double d[3];
+        double r2 = separation(pos + 4 * i, pos + 4 * j, L, d);
+        double q = r2 / (R0 * R0);
+        if (!(q < 1.0)) {
+            broken++;
+            continue;
+        }
+        double fr = -K / (1.0 - q);
+        double v = -0.5 * K * R0 * R0 * log(1.0 - q);
+        double f[3] = {fr * d[0], fr * d[1], fr * d[2]};
+        for (int k = 0; k < 3; k++) {
+            force[4 * i + k] += f[k];
+            force[4 * j + k] -= f[k];
+        }
+        force[4 * i + 3] += 0.5 * v;
+        force[4 * j + 3] += 0.5 * v;
+        if (virial) {
+            double w[6] = {d[0] * f[0], d[0] * f[1], d[0] * f[2],
+                           d[1] * f[1], d[1] * f[2], d[2] * f[2]};
+            for (int k = 0; k < 6; k++) {
+                virial[6 * i + k] += 0.5 * w[k];
+                virial[6 * j + k] += 0.5 * w[k];
+            }
+        }
+        if (absf) {
+            double m = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+            absf[i] += m;
+            absf[j] += m;
+        }
+    }
+    return broken;
+}
+
 void orc_bond_forces(int64_t n_bonds, const int32_t *bonds, const double *pos,
                      const double *L, double K, double r0, double *force,
                      double *virial, double *absf) {
@@ -704,7 +747,12 @@ static void compute_forces(int64_t n, const double *pos, const double *vel,
                              p->kT, p->dt, step, p->seed, counts, rows, p->max_nb, force,
                              virial, NULL);
     if (p->n_bonds > 0)
-        orc_bond_forces(p->n_bonds, p->bonds, pos, p->L, p->K, p->r0, force, virial, NULL);
+    {
+        if (p->bond_style == 1)
+            orc_fene_bond_forces(p->n_bonds, p->bonds, pos, p->L, p->K, p->r0, force, virial, NULL);
+        else
+            orc_bond_forces(p->n_bonds, p->bonds, pos, p->L, p->K, p->r0, force, virial, NULL);
+    }
 }
 
 int64_t orc_run(int64_t n, double *pos, double *vel, int32_t *image,

@@ -131,6 +131,12 @@ void orc_dpd_forces_nlist(int64_t n, const double *pos, const double *vel,
 /* Harmonic bonds V = K/2 (r - r0)^2 between particle indices bonds[2b],
  * bonds[2b+1].  ADDS to force (and PE in force w, half per end), virial, absf
  * (any of virial / absf may be NULL). */
+/* FENE bonds: V = -K R0^2 / 2 ln(1 - (r/R0)^2); returns the number of
+ * bonds at r >= R0 (skipped). */
+int64_t orc_fene_bond_forces(int64_t n_bonds, const int32_t *bonds, const double *pos,
+                             const double *L, double K, double R0, double *force,
+                             double *virial, double *absf);
+
 void orc_bond_forces(int64_t n_bonds, const int32_t *bonds, const double *pos,
                      const double *L, double K, double r0, double *force,
                      double *virial, double *absf);
@@ -207,6 +213,7 @@ typedef struct {
     double t_tau;          /* Nose-Hoover period */
     uint64_t t_seed;       /* Langevin noise key */
     double *nh_state;      /* Nose-Hoover {xi, eta}, updated in place (or NULL) */
+    int32_t bond_style;    /* 0 = harmonic (K, r0), 1 = FENE (K, R0 = r0) */
 } orc_params;
 
 /* Whole MD loop: forces at step0, then n_steps steps of the chosen

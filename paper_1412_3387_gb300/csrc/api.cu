@@ -384,6 +384,7 @@ const char *md_status_string(md_status s) {
     case MD_ERR_CELL_OVERFLOW: return "cell occupancy above the in-cell sort limit";
     case MD_ERR_STATE: return "call not valid in the current state";
     case MD_ERR_TIMEOUT: return "a kernel's internal wait timed out (internal error)";
+    case MD_ERR_BOND: return "a FENE bond reached its maximum extension";
   }
   return "unknown status";
 }
@@ -692,6 +693,7 @@ md_status md_set_bonds(md_system *s, const int32_t *bond_tags, int64_t n_bonds, 
   if (!s || n_bonds < 0 || (n_bonds > 0 && !bond_tags)) return MD_ERR_INVALID_ARG;
   if (n_bonds > 0 && s->p.max_bonds == 0) return MD_ERR_INVALID_ARG;
   if (!(K >= 0) || !(r0 >= 0)) return MD_ERR_INVALID_ARG;
+  if (s->a.bond_style == MD_BOND_FENE && !(r0 > 0)) return MD_ERR_INVALID_ARG;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   const int64_t N = s->a.n;
   const int mb = s->p.max_bonds;
@@ -714,6 +716,15 @@ md_status md_set_bonds(md_system *s, const int32_t *bond_tags, int64_t n_bonds, 
   s->a.bond_r0 = r0;
   s->gvalid = false;
   s->built = false;  // forces must include the bonds before the next step
+  return MD_OK;
+}
+
+md_status md_set_bond_style(md_system *s, int32_t style) {
+  if (!s || (style != MD_BOND_HARMONIC && style != MD_BOND_FENE)) return MD_ERR_INVALID_ARG;
+  if (style == MD_BOND_FENE && !(s->a.bond_r0 > 0)) return MD_ERR_INVALID_ARG;
+  s->a.bond_style = style;
+  s->gvalid = false;
+  s->built = false;  // forces must include the bonds of the new style
   return MD_OK;
 }
 
@@ -1022,6 +1033,10 @@ md_status md_poll_error(md_system *s, int64_t *detail) {
   if (ds.error & kErrNonfinite) {
     if (detail) *detail = ds.error_detail;
     return MD_ERR_NONFINITE;
+  }
+  if (ds.error & kErrBond) {
+    if (detail) *detail = ds.error_detail;
+    return MD_ERR_BOND;
   }
   if (ds.error & kErrCellOverflow) return MD_ERR_CELL_OVERFLOW;
   if (ds.error & kErrStaleList) return MD_ERR_STATE;

@@ -337,18 +337,28 @@ __global__ void k_bonds(KArgs a) {
     const int32_t j = a.rtag[p];
     double d[3];
     const double r2 = exact_r2(pi, ld_d4(a.pos + j), rp, d);
-    double fr, dr;
-    if (a.bond_r0 == 0.0) {
+    double fr, v = 0.0;
+    if (a.bond_style == MD_BOND_FENE) {
+      // FENE: V = -K R0^2 / 2 ln(1 - q), q = (r / R0)^2; -dV/dr / r = -K / (1 - q)
+      const double q = r2 / (a.bond_r0 * a.bond_r0);
+      if (!(q < 1.0)) {
+        if (atomicOr(&a.ds->error, kErrBond) == 0u) a.ds->error_detail = i;
+        continue;
+      }
+      fr = -a.bond_K / (1.0 - q);
+      if (ENERGY) v = -0.5 * a.bond_K * a.bond_r0 * a.bond_r0 * log(1.0 - q);
+    } else if (a.bond_r0 == 0.0) {
       fr = -a.bond_K;
-      dr = sqrt(r2);
+      if (ENERGY) v = 0.5 * a.bond_K * r2;
     } else {
-      dr = sqrt(r2);
+      const double dr = sqrt(r2);
       fr = dr > 0.0 ? -a.bond_K * (dr - a.bond_r0) / dr : 0.0;
+      if (ENERGY) v = 0.5 * a.bond_K * (dr - a.bond_r0) * (dr - a.bond_r0);
     }
     const double fx = fr * d[0], fy = fr * d[1], fz = fr * d[2];
     f[0] += fx; f[1] += fy; f[2] += fz;
     if (ENERGY) {
-      pe += 0.25 * a.bond_K * (dr - a.bond_r0) * (dr - a.bond_r0);
+      pe += 0.5 * v;
       w[0] += 0.5 * d[0] * fx; w[1] += 0.5 * d[0] * fy; w[2] += 0.5 * d[0] * fz;
       w[3] += 0.5 * d[1] * fy; w[4] += 0.5 * d[1] * fz; w[5] += 0.5 * d[2] * fz;
     }

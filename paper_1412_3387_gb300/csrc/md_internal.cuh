@@ -29,6 +29,7 @@ enum : uint32_t {
   kErrBadInput = 1u << 3,
   kErrTimeout = 1u << 4,
   kErrStaleList = 1u << 5,  // pair forces asked for before the list of a new binning
+  kErrBond = 1u << 6,       // a FENE bond at or beyond its maximum extension
 };
 
 // Per-replica constants (device-resident copy + host mirror).
@@ -170,6 +171,7 @@ struct KArgs {
   double dt, mass, kT;
   double half_dt_m;    // dt / (2 m), computed once on the host
   double bond_K, bond_r0;
+  int32_t bond_style;  // md_bond_style
   // thermostat (md_set_integrator)
   int32_t integ;         // md_integrator
   double t_kT, t_c, t_sig, t_tau;  // kT; Langevin exp(-gamma dt), sqrt((1 - c^2) kT / m); NH tau

@@ -348,7 +348,9 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
     }
   } else {
     dp.oi = oi;
-    dp.half = a.half != 0;
+    // idle lanes of a short group shadow its first particle's row: only the
+    // lanes of real particles may add to partners
+    dp.half = a.half != 0 && active;
     dp.ti = cell_type(__float_as_uint(oi.w));
     dp.ident = ident;
     dp.pi = ld_d4(a.pos + i);
@@ -542,7 +544,7 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
 #pragma unroll
       for (int c = 0; c < 6; c++) dw[c] = seg_sum<W>(dw[c]);
     }
-    if (active && sl == 0 && dp.half) {
+    if (active && sl == 0 && a.half) {
       // half list: partners add into this particle concurrently
       double *f = reinterpret_cast<double *>(a.force) + 4 * (int64_t)i;
       atomicAdd(f + 0, df[0]);

@@ -80,6 +80,7 @@ SIGNATURES = {
     "md_lj_forces_noalloc": (C.c_int, [_P, _I64, _P, _D, _D, _D, _P, _P]),
     "md_set_integrator": (C.c_int, [_P, _I32, _D, _D, C.c_uint64]),
     "md_set_newton": (C.c_int, [_P, _I32]),
+    "md_set_bond_style": (C.c_int, [_P, _I32]),
     "md_get_thermostat": (C.c_int, [_P, _P]),
 }
 INTEGRATORS = {"nve": 0, "langevin": 1, "nose-hoover": 2}
@@ -270,6 +271,12 @@ class MDSystem:
         check(self.lib.md_reduce_thermo(self.handle, _ptr(out), _stream(stream)),
               "md_reduce_thermo")
         return out
+
+    def set_bond_style(self, style="harmonic"):
+        """"harmonic" or "fene" (the r0 of set_bonds is then R0); see
+        md_set_bond_style."""
+        check(self.lib.md_set_bond_style(self.handle, {"harmonic": 0, "fene": 1}[style]),
+              "md_set_bond_style")
 
     def set_newton(self, enable=True):
         """Half neighbour list with Newton's third law (FP64 systems); see

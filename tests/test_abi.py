@@ -37,8 +37,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.md_abi_version() == 5
-    for code in range(10):
+    assert lib.md_abi_version() == 6
+    for code in range(11):
         assert lib.md_status_string(code)
 
 

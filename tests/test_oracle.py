@@ -395,6 +395,54 @@ def test_harmonic_dimer_oscillation_period():
     assert abs(vel[0, 0]) < 0.01
 
 
+def test_fene_bond_closed_forms_and_stretch():
+    """FENE (Sec. 3 lists FENE bonds): |F| = K r / (1 - (r/R0)^2), so 2 K R0 / 3
+    at r = R0/2; V(R0/sqrt 2) = K R0^2 ln2 / 2; -dV/dr by central differences;
+    attractive along the bond; a bond at r >= R0 is counted and skipped."""
+    K, R0 = 30.0, 1.5
+    L = np.array([20.0, 20.0, 20.0])
+    pos = np.zeros((2, 4))
+    pos[0, :3] = [5.0, 5.0, 5.0]
+    pos[1, :3] = [5.0 + R0 / 2, 5.0, 5.0]
+    f, _, _, nb = oracle.fene_bond_forces([[0, 1]], pos, L, K, R0)
+    assert nb == 0
+    assert f[0, 0] == pytest.approx(2 * K * R0 / 3, rel=1e-14)  # pulled toward particle 1
+    assert f[1, 0] == pytest.approx(-2 * K * R0 / 3, rel=1e-14)
+    pos[1, :3] = [5.0, 5.0 + R0 / math.sqrt(2), 5.0]
+    f, _, _, _ = oracle.fene_bond_forces([[0, 1]], pos, L, K, R0)
+    assert f[:, 3].sum() == pytest.approx(0.5 * K * R0 * R0 * math.log(2), rel=1e-14)
+    for r in (0.3, 0.9, 1.3):
+        h = 1e-6
+        e = []
+        for x in (r - h, r + h, r):
+            pos[1, :3] = [5.0 + x, 5.0, 5.0]
+            f, _, _, _ = oracle.fene_bond_forces([[0, 1]], pos, L, K, R0)
+            e.append((f[:, 3].sum(), f[1, 0]))
+        assert e[2][1] == pytest.approx(-(e[1][0] - e[0][0]) / (2 * h), rel=1e-7)
+    pos[1, :3] = [5.0 + R0, 5.0, 5.0]
+    f, _, _, nb = oracle.fene_bond_forces([[0, 1]], pos, L, K, R0)
+    assert nb == 1 and not f.any()
+
+
+def test_fene_dimer_small_oscillation_period():
+    """For r << R0 the FENE bond is a harmonic spring of constant K: a dimer
+    oscillating through r = 0 has period 2 pi / sqrt(2 K / m) (through the
+    oracle's MD loop with the FENE bond style; the pair potential has eps = 0)."""
+    K, R0, dt = 4.0, 10.0, 1e-3
+    L = 12.0
+    pos = np.zeros((2, 4))
+    vel = np.zeros((2, 4))
+    pos[0, :3] = [6.0, 6.0, 6.0]
+    pos[1, :3] = [6.2, 6.0, 6.0]
+    img = np.zeros((2, 4), np.int32)
+    period = 2 * math.pi / math.sqrt(2 * K)
+    n = int(round(period / dt))
+    out = oracle.run(pos, vel, img, L, n, r_cut=2.5, r_skin=0.3, dt=dt, coeff=[[0.0, 1.0]],
+                     bonds=[[0, 1]], K=K, r0=R0, bond_style="fene", max_nb=4)
+    sep = out["pos"][1, 0] - out["pos"][0, 0]
+    assert sep == pytest.approx(0.2, abs=5e-4)  # back after one period (anharmonic ~(r/R0)^2)
+
+
 def test_vv_first_wraps_and_counts_images():
     L = np.array([10.0, 10.0, 10.0])
     pos = np.array([[9.95, 0.02, 5.0, 0.0]])
