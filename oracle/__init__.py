@@ -51,6 +51,8 @@ class Params(C.Structure):
         ("max_nb", C.c_int32), ("integrator", C.c_int32), ("t_kT", C.c_double),
         ("t_gamma", C.c_double), ("t_tau", C.c_double), ("t_seed", C.c_uint64),
         ("nh_state", C.c_void_p), ("bond_style", C.c_int32),
+        ("n_angles", C.c_int64), ("angles", C.c_void_p), ("angle_K", C.c_double),
+        ("angle_theta0", C.c_double),
     ]
 
 
@@ -80,6 +82,7 @@ def lib():
                 "orc_dpd_forces_nlist": (None, [I64, P, P, P, P, P, D, I32, P, D, D, U64, U64, P, P, I32, P, P, P]),
                 "orc_bond_forces": (None, [I64, P, P, P, D, D, P, P, P]),
                 "orc_fene_bond_forces": (I64, [I64, P, P, P, D, D, P, P, P]),
+                "orc_angle_forces": (None, [I64, P, P, P, D, D, P, P, P]),
                 "orc_vv_first": (None, [I64, P, P, P, P, D, D, P]),
                 "orc_vv_second": (None, [I64, P, P, D, D]),
                 "orc_thermo": (None, [I64, P, P, P, D, P, P]),
@@ -284,6 +287,20 @@ def fene_bond_forces(bonds, pos, L, K, R0, force=None, virial=None, absf=None):
     return force, virial, absf, int(broken)
 
 
+def angle_forces(angles, pos, L, K, theta0, force=None, virial=None, absf=None):
+    """Adds harmonic-angle forces (index triplets, vertex in the middle) to
+    (force, virial, absf); returns them."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    tri = _i32(angles).reshape(-1, 3)
+    force = np.zeros((n, 4)) if force is None else _f64(force).copy()
+    virial = np.zeros((n, 6)) if virial is None else _f64(virial).copy()
+    absf = np.zeros(n) if absf is None else _f64(absf).copy()
+    lib().orc_angle_forces(tri.shape[0], _p(tri), _p(pos), _p(_box(L)), float(K), float(theta0),
+                           _p(force), _p(virial), _p(absf))
+    return force, virial, absf
+
+
 def vv_first(pos, vel, image, force, dt, L, mass=1.0):
     pos, vel, force = _f64(pos).copy(), _f64(vel).copy(), _f64(force)
     image = _i32(image).copy()
@@ -354,7 +371,7 @@ def run(pos, vel, image, L, n_steps, *, r_cut, r_skin, dt, pair="lj", type=None,
         tag=None, coeff=((1.0, 1.0),), kT=1.0, seed=0, mass=1.0, shift_energy=False,
         thermo_period=0, bonds=None, K=0.0, r0=0.0, step0=0, max_nb=256,
         integrator="nve", t_kT=1.0, gamma=1.0, tau=1.0, t_seed=0, nh_state=None,
-        bond_style="harmonic"):
+        bond_style="harmonic", angles=None, angle_K=0.0, angle_theta0=0.0):
     """Full MD loop on copies of the inputs; returns a dict with the final
     state, forces, thermo rows, the number of list builds and (Nose-Hoover)
     the thermostat state [xi, eta] (nh_state gives its initial value)."""
@@ -387,6 +404,10 @@ def run(pos, vel, image, L, n_steps, *, r_cut, r_skin, dt, pair="lj", type=None,
     nh = np.ascontiguousarray(np.zeros(2) if nh_state is None else nh_state, np.float64).copy()
     p.nh_state = nh.ctypes.data
     p.bond_style = {"harmonic": 0, "fene": 1}[bond_style]
+    tri = _i32(np.zeros((0, 3)) if angles is None else angles).reshape(-1, 3)
+    p.n_angles = tri.shape[0]
+    p.angles = tri.ctypes.data if tri.shape[0] else None
+    p.angle_K, p.angle_theta0 = float(angle_K), float(angle_theta0)
     n_th = (n_steps // thermo_period + 1) if thermo_period else 0
     th = np.zeros((max(n_th, 1), 8))
     builds = lib().orc_run(n, _p(pos), _p(vel), _p(image), _p(t), _p(g), _p(force),

@@ -513,6 +513,55 @@ int64_t orc_fene_bond_forces(int64_t n_bonds, const int32_t *bonds, const double
     return broken;
 }
 
+/* Harmonic angle (Sec. 3 lists harmonic angle potentials): for a triplet
+ * (a, b, c) with vertex b, u = x_a - x_b and w = x_c - x_b (minimum image),
+ * theta = acos(u.w / (|u| |w|)) and V = K/2 (theta - theta0)^2.  With
+ * c = cos(theta) and s = sin(theta):
+ *   F_a = K (theta - theta0) / s (w / (|u| |w|) - c u / |u|^2),
+ *   F_c = K (theta - theta0) / s (u / (|u| |w|) - c w / |w|^2),
+ *   F_b = -(F_a + F_c).
+ * Each particle of the triplet gets a third of V and of the angle's virial
+ * u (x) F_a + w (x) F_c.  s is floored at 1e-12 (a straight or folded
+ * triplet). */
+void orc_angle_forces(int64_t n_angles, const int32_t *tri, const double *pos,
+                      const double *L, double K, double theta0, double *force,
+                      double *virial, double *absf) {
+    for (int64_t t = 0; t < n_angles; t++) {
+        int64_t a = tri[3 * t], b = tri[3 * t + 1], c = tri[3 * t + 2];
+        double u[3], w[3];
+        double uu = separation(pos + 4 * a, pos + 4 * b, L, u);
+        double ww = separation(pos + 4 * c, pos + 4 * b, L, w);
+        double ru = sqrt(uu), rw = sqrt(ww);
+        double cs = (u[0] * w[0] + u[1] * w[1] + u[2] * w[2]) / (ru * rw);
+        if (cs > 1.0) cs = 1.0;
+        if (cs < -1.0) cs = -1.0;
+        double th = acos(cs);
+        double sn = sqrt(1.0 - cs * cs);
+        if (sn < 1e-12) sn = 1e-12;
+        double g = K * (th - theta0) / sn;
+        double fa[3], fc[3], fb[3];
+        for (int k = 0; k < 3; k++) {
+            fa[k] = g * (w[k] / (ru * rw) - cs * u[k] / uu);
+            fc[k] = g * (u[k] / (ru * rw) - cs * w[k] / ww);
+            fb[k] = -(fa[k] + fc[k]);
+        }
+        double v = 0.5 * K * (th - theta0) * (th - theta0);
+        double vir[6] = {u[0] * fa[0] + w[0] * fc[0], u[0] * fa[1] + w[0] * fc[1],
+                         u[0] * fa[2] + w[0] * fc[2], u[1] * fa[1] + w[1] * fc[1],
+                         u[1] * fa[2] + w[1] * fc[2], u[2] * fa[2] + w[2] * fc[2]};
+        int64_t who[3] = {a, b, c};
+        double *fs[3] = {fa, fb, fc};
+        for (int m = 0; m < 3; m++) {
+            for (int k = 0; k < 3; k++) force[4 * who[m] + k] += fs[m][k];
+            force[4 * who[m] + 3] += v / 3.0;
+            if (virial)
+                for (int k = 0; k < 6; k++) virial[6 * who[m] + k] += vir[k] / 3.0;
+            if (absf)
+                absf[who[m]] += sqrt(fs[m][0] * fs[m][0] + fs[m][1] * fs[m][1] + fs[m][2] * fs[m][2]);
+        }
+    }
+}
+
 void orc_bond_forces(int64_t n_bonds, const int32_t *bonds, const double *pos,
                      const double *L, double K, double r0, double *force,
                      double *virial, double *absf) {
@@ -753,6 +802,9 @@ static void compute_forces(int64_t n, const double *pos, const double *vel,
         else
             orc_bond_forces(p->n_bonds, p->bonds, pos, p->L, p->K, p->r0, force, virial, NULL);
     }
+    if (p->n_angles > 0)
+        orc_angle_forces(p->n_angles, p->angles, pos, p->L, p->angle_K, p->angle_theta0, force,
+                         virial, NULL);
 }
 
 int64_t orc_run(int64_t n, double *pos, double *vel, int32_t *image,

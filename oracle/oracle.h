@@ -137,6 +137,12 @@ int64_t orc_fene_bond_forces(int64_t n_bonds, const int32_t *bonds, const double
                              const double *L, double K, double R0, double *force,
                              double *virial, double *absf);
 
+/* Harmonic angles V = K/2 (theta - theta0)^2 over triplets (a, b, c) with
+ * vertex b; each particle gets a third of V and of the angle's virial. */
+void orc_angle_forces(int64_t n_angles, const int32_t *tri, const double *pos,
+                      const double *L, double K, double theta0, double *force,
+                      double *virial, double *absf);
+
 void orc_bond_forces(int64_t n_bonds, const int32_t *bonds, const double *pos,
                      const double *L, double K, double r0, double *force,
                      double *virial, double *absf);
@@ -214,6 +220,9 @@ typedef struct {
     uint64_t t_seed;       /* Langevin noise key */
     double *nh_state;      /* Nose-Hoover {xi, eta}, updated in place (or NULL) */
     int32_t bond_style;    /* 0 = harmonic (K, r0), 1 = FENE (K, R0 = r0) */
+    int64_t n_angles;      /* harmonic angles (index triplets, vertex in the middle) */
+    const int32_t *angles;
+    double angle_K, angle_theta0;
 } orc_params;
 
 /* Whole MD loop: forces at step0, then n_steps steps of the chosen

@@ -443,6 +443,69 @@ def test_fene_dimer_small_oscillation_period():
     assert sep == pytest.approx(0.2, abs=5e-4)  # back after one period (anharmonic ~(r/R0)^2)
 
 
+def test_harmonic_angle_gradient_invariances_and_values():
+    """Harmonic angles (Sec. 3): forces equal -grad of the total energy by
+    central differences; zero net force and torque; a right angle with
+    theta0 = 0 has V = K/2 (pi/2)^2 split in thirds; theta = theta0 gives no
+    force; the virial trace is sum x . F."""
+    rng = np.random.default_rng(8)
+    L = np.array([30.0, 30.0, 30.0])
+    K, th0 = 7.0, 1.9
+    for _ in range(5):
+        pos = np.zeros((3, 4))
+        pos[:, :3] = 15.0 + rng.normal(scale=0.8, size=(3, 3))
+        f, vir, _ = oracle.angle_forces([[0, 1, 2]], pos, L, K, th0)
+        assert np.abs(f[:, :3].sum(axis=0)).max() < 1e-12 * np.abs(f[:, :3]).max()
+        torque = np.cross(pos[:, :3], f[:, :3]).sum(axis=0)
+        assert np.abs(torque).max() < 1e-10 * np.abs(f[:, :3]).max() * 15
+        assert np.sum(vir[:, [0, 3, 5]]) == pytest.approx(np.sum(pos[:, :3] * f[:, :3]), rel=1e-10)
+        h = 1e-6
+        for m in range(3):
+            for k in range(3):
+                pp, pm = pos.copy(), pos.copy()
+                pp[m, k] += h
+                pm[m, k] -= h
+                ep = oracle.angle_forces([[0, 1, 2]], pp, L, K, th0)[0][:, 3].sum()
+                em = oracle.angle_forces([[0, 1, 2]], pm, L, K, th0)[0][:, 3].sum()
+                assert f[m, k] == pytest.approx(-(ep - em) / (2 * h), rel=1e-6, abs=1e-8)
+    pos = np.zeros((3, 4))
+    pos[:, :3] = [[16.0, 15.0, 15.0], [15.0, 15.0, 15.0], [15.0, 17.0, 15.0]]
+    f, _, _ = oracle.angle_forces([[0, 1, 2]], pos, L, K, 0.0)
+    assert f[:, 3] == pytest.approx([K / 2 * (math.pi / 2) ** 2 / 3] * 3, rel=1e-14)
+    f, _, _ = oracle.angle_forces([[0, 1, 2]], pos, L, K, math.pi / 2)
+    assert np.abs(f).max() < 1e-14
+
+
+def test_chain_with_angles_conserves_energy():
+    """A bonded, angled chain (no pair forces in range of eps = 0) in the
+    oracle's MD loop: energy stays constant to O(dt^2) (halving dt quarters
+    the energy error), which pins the angle forces inside the loop."""
+    L = 20.0
+    n = 8
+    pos = np.zeros((n, 4))
+    pos[:, 0] = 6.0 + 0.9 * np.arange(n)
+    pos[:, 1] = 10.0 + 0.3 * np.sin(np.arange(n))
+    pos[:, 2] = 10.0
+    rng = np.random.default_rng(3)
+    vel = np.zeros((n, 4))
+    vel[:, :3] = rng.normal(scale=0.3, size=(n, 3))
+    vel[:, :3] -= vel[:, :3].mean(axis=0)
+    img = np.zeros((n, 4), np.int32)
+    bonds = [[i, i + 1] for i in range(n - 1)]
+    angles = [[i, i + 1, i + 2] for i in range(n - 2)]
+    errs = []
+    for dt in (0.004, 0.002):
+        steps = int(round(2.0 / dt))
+        out = oracle.run(pos, vel, img, L, steps, r_cut=2.5, r_skin=0.3, dt=dt,
+                         coeff=[[0.0, 1.0]], bonds=bonds, K=20.0, r0=0.9, angles=angles,
+                         angle_K=5.0, angle_theta0=2.6, thermo_period=int(round(0.1 / dt)),
+                         max_nb=16)
+        e = out["thermo"][:, 0] + out["thermo"][:, 1]
+        errs.append(np.max(np.abs(e - e[0])))
+    assert errs[0] < 1e-2
+    assert errs[1] == pytest.approx(errs[0] / 4, rel=0.25)
+
+
 def test_vv_first_wraps_and_counts_images():
     L = np.array([10.0, 10.0, 10.0])
     pos = np.array([[9.95, 0.02, 5.0, 0.0]])
