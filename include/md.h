@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 6
+#define MD_ABI_VERSION 7
 
 typedef struct md_system md_system;
 typedef struct CUstream_st *md_stream; /* a cudaStream_t; NULL = legacy default stream */
@@ -123,6 +123,8 @@ typedef struct {
     int32_t graph_steps;           /* md_run: steps per captured CUDA graph
                                       (multiple of thermo_period); 0 = eager */
     int32_t max_bonds;             /* bonds per particle capacity; 0 = no bonds */
+    int32_t max_angles;            /* angles per particle capacity (as an end or the
+                                      vertex); 0 = no angles */
 } md_params;
 
 /* Thermodynamic row per replica, 8 doubles (Sec. 4.3.3 groups these global
@@ -164,6 +166,20 @@ md_status md_destroy_system(md_system *s);
  * max_bonds partners.  Synchronises `stream`. */
 md_status md_set_bonds(md_system *s, const int32_t *bond_tags, int64_t n_bonds,
                        double K, double r0, md_stream stream);
+
+/* Harmonic angles V = K/2 (theta - theta0)^2 (Sec. 3 lists harmonic angle
+ * potentials; Sec. 4.3.4 treats angles like bonds, as groups of particle
+ * IDs).  angle_tags: HOST [n_angles][3] particle IDs (a, b, c), b the
+ * vertex, theta the angle between x_a - x_b and x_c - x_b (minimum image);
+ * K >= 0, 0 <= theta0 <= pi.  Stores, per particle ID, the angles it takes
+ * part in; each particle then sums its own force from them (no atomics),
+ * and gets a third of each angle's energy and virial.  The forces are added
+ * with the bonds' (md_compute_bonds, md_step, md_run).  Errors:
+ * MD_ERR_INVALID_ARG (bad IDs, repeated IDs in a triplet, a particle in more
+ * than max_angles angles, K or theta0 out of range).  Synchronises
+ * `stream`. */
+md_status md_set_angles(md_system *s, const int32_t *angle_tags, int64_t n_angles,
+                        double K, double theta0, md_stream stream);
 
 /* Bond style of md_set_bonds' bonds (Sec. 3 lists harmonic and FENE bonds):
  *   MD_BOND_HARMONIC  V = K/2 (r - r0)^2 (the default)

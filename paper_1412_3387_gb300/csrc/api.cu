@@ -33,6 +33,7 @@ struct md_system {
   bool bin_all = false, bin_cond = false;
   int64_t step = 0;
   int64_t n_bonds = 0;
+  int64_t n_angles = 0;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool gvalid = false;
@@ -96,7 +97,7 @@ struct Plan {
       o_brick_rep, o_brick_desc, o_cell_count, o_cell_start,
       o_chunk_sum, o_cell_idx, o_cellpos, o_pcell, o_pslot, o_n_nb, o_rtag, o_pos4f, o_oref, o_vel4f,
       o_nl, o_nl_tiles, o_force, o_virial, o_tpart, o_ds, o_rebuild, o_sort_now, o_last_sort, o_ident,
-      o_list_ok, o_coeff, o_btab, o_s_pos, o_s_vel, o_s_img, o_s_tag, o_s_type, o_s_oref, o_nh,
+      o_list_ok, o_coeff, o_btab, o_atab, o_s_pos, o_s_vel, o_s_img, o_s_tag, o_s_type, o_s_oref, o_nh,
       o_nh_part;
   size_t total = 0;
 };
@@ -123,7 +124,8 @@ md_status validate(const md_params *p) {
   for (int k = 0; k < pair_ncoeff(p->pair) * p->n_types * p->n_types; k++)
     if (!std::isfinite(p->pair_coeff[k])) return MD_ERR_INVALID_ARG;
   if (p->max_nb < 1 || p->max_nb > (1 << 20)) return MD_ERR_INVALID_ARG;
-  if (p->sort_period < 0 || p->thermo_period < 0 || p->graph_steps < 0 || p->max_bonds < 0)
+  if (p->sort_period < 0 || p->thermo_period < 0 || p->graph_steps < 0 || p->max_bonds < 0 ||
+      p->max_angles < 0 || p->max_angles > 64)
     return MD_ERR_INVALID_ARG;
   if (p->graph_steps > 0 && p->thermo_period > 0 && p->graph_steps % p->thermo_period != 0)
     return MD_ERR_INVALID_ARG;
@@ -278,6 +280,7 @@ md_status make_plan(const md_params *p, Plan &pl) {
   pl.o_list_ok = take(sizeof(int32_t) * R);
   pl.o_coeff = take(64 * (size_t)p->n_types * p->n_types);
   pl.o_btab = take(sizeof(int32_t) * (size_t)std::max(p->max_bonds, 0) * N);
+  pl.o_atab = take(sizeof(int32_t) * 3 * (size_t)std::max(p->max_angles, 0) * N);
   pl.o_s_pos = take(sizeof(double4) * N);
   pl.o_s_vel = take(sizeof(double4) * N);
   pl.o_s_img = take(sizeof(int4) * N);
@@ -310,7 +313,7 @@ md_status enqueue_step(md_system *s, int want_virial, cudaStream_t st, bool fold
   if (s->p.sort_period > 0) MD_CUDA(launch_sort(a, 0, st));
   MD_CUDA(launch_nlist(a, s->tune[MD_KERNEL_NLIST], 0, st));
   MD_CUDA(launch_pair(a, s->tune[MD_KERNEL_PAIR], want_virial, st));
-  if (s->n_bonds > 0) MD_CUDA(launch_bonds(a, want_virial, st));
+  if (s->n_bonds > 0 || s->n_angles > 0) MD_CUDA(launch_bonds(a, want_virial, st));
   if (close) MD_CUDA(launch_integrate2(a, st));
   return MD_OK;
 }
@@ -322,7 +325,7 @@ md_status prepare(md_system *s, cudaStream_t st) {
   MD_CUDA(launch_nlist(s->a, s->tune[MD_KERNEL_NLIST], 1, st));
   s->listed = true;
   MD_CUDA(launch_pair(s->a, s->tune[MD_KERNEL_PAIR], 0, st));
-  if (s->n_bonds > 0) MD_CUDA(launch_bonds(s->a, 0, st));
+  if (s->n_bonds > 0 || s->n_angles > 0) MD_CUDA(launch_bonds(s->a, 0, st));
   s->built = true;
   return MD_OK;
 }
@@ -481,6 +484,8 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   a.list_ok = at<int32_t>(ws, pl.o_list_ok);
   a.rtag = at<int32_t>(ws, pl.o_rtag);
   a.btab = p->max_bonds > 0 ? at<int32_t>(ws, pl.o_btab) : nullptr;
+  a.atab = p->max_angles > 0 ? at<int32_t>(ws, pl.o_atab) : nullptr;
+  a.max_angles = p->max_angles;
   a.s_pos = at<double4>(ws, pl.o_s_pos);
   a.s_vel = at<double4>(ws, pl.o_s_vel);
   a.s_img = at<int4>(ws, pl.o_s_img);
@@ -667,6 +672,10 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   if (p->max_bonds > 0 &&
       cudaMemsetAsync(at<void>(ws, pl.o_btab), 0xff, sizeof(int32_t) * (size_t)p->max_bonds * pl.n, stream))
     return fail(MD_ERR_CUDA);
+  if (p->max_angles > 0 &&
+      cudaMemsetAsync(at<void>(ws, pl.o_atab), 0xff, sizeof(int32_t) * 3 * (size_t)p->max_angles * pl.n,
+                      stream))
+    return fail(MD_ERR_CUDA);
   if (launch_init_frames(a, stream) != cudaSuccess) return fail(MD_ERR_CUDA);
   if (launch_nh_reset(a, stream) != cudaSuccess) return fail(MD_ERR_CUDA);
   if (cudaStreamSynchronize(stream) != cudaSuccess) return fail(MD_ERR_CUDA);
@@ -716,6 +725,42 @@ md_status md_set_bonds(md_system *s, const int32_t *bond_tags, int64_t n_bonds, 
   s->a.bond_r0 = r0;
   s->gvalid = false;
   s->built = false;  // forces must include the bonds before the next step
+  return MD_OK;
+}
+
+md_status md_set_angles(md_system *s, const int32_t *angle_tags, int64_t n_angles, double K,
+                        double theta0, md_stream stream_) {
+  if (!s || n_angles < 0 || (n_angles > 0 && !angle_tags)) return MD_ERR_INVALID_ARG;
+  if (n_angles > 0 && s->p.max_angles == 0) return MD_ERR_INVALID_ARG;
+  if (!(K >= 0) || !std::isfinite(K) || !(theta0 >= 0) || !(theta0 <= 3.14159265358979324))
+    return MD_ERR_INVALID_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  const int64_t N = s->a.n;
+  const int ma = s->p.max_angles;
+  if (ma > 0) {
+    std::vector<int32_t> tab((size_t)N * ma * 3, -1);
+    std::vector<int32_t> cnt(N, 0);
+    for (int64_t t = 0; t < n_angles; t++) {
+      const int32_t *q = angle_tags + 3 * t;
+      for (int k = 0; k < 3; k++)
+        if (q[k] < 0 || q[k] >= N) return MD_ERR_INVALID_ARG;
+      if (q[0] == q[1] || q[1] == q[2] || q[0] == q[2]) return MD_ERR_INVALID_ARG;
+      for (int k = 0; k < 3; k++) {
+        const int32_t x = q[k];
+        if (cnt[x] >= ma) return MD_ERR_INVALID_ARG;
+        int32_t *e = tab.data() + ((size_t)x * ma + cnt[x]++) * 3;
+        e[0] = q[0], e[1] = q[1], e[2] = q[2];
+      }
+    }
+    MD_CUDA(cudaMemcpyAsync(s->a.atab, tab.data(), sizeof(int32_t) * tab.size(),
+                            cudaMemcpyHostToDevice, stream));
+    MD_CUDA(cudaStreamSynchronize(stream));
+  }
+  s->n_angles = n_angles;
+  s->a.angle_K = K;
+  s->a.angle_th0 = theta0;
+  s->gvalid = false;
+  s->built = false;  // forces must include the angles before the next step
   return MD_OK;
 }
 
@@ -772,7 +817,7 @@ md_status md_compute_pair(md_system *s, int32_t want_virial, md_stream stream) {
 
 md_status md_compute_bonds(md_system *s, int32_t want_virial, md_stream stream) {
   if (!s) return MD_ERR_INVALID_ARG;
-  if (s->n_bonds == 0) return MD_OK;
+  if (s->n_bonds == 0 && s->n_angles == 0) return MD_OK;
   MD_CUDA(launch_bonds(s->a, want_virial ? 1 : 0, reinterpret_cast<cudaStream_t>(stream)));
   return MD_OK;
 }
@@ -998,7 +1043,7 @@ md_status md_autotune(md_system *s, int32_t n_samples, int32_t block_stride, md_
   s->tune[MD_KERNEL_NLIST] = best_nl;
   if (result == MD_OK && launch_nlist(s->a, best_nl, 1, st) != cudaSuccess) result = MD_ERR_CUDA;
   if (result == MD_OK && launch_pair(s->a, best_pair, 0, st) != cudaSuccess) result = MD_ERR_CUDA;
-  if (result == MD_OK && s->n_bonds > 0 && launch_bonds(s->a, 0, st) != cudaSuccess) result = MD_ERR_CUDA;
+  if (result == MD_OK && (s->n_bonds > 0 || s->n_angles > 0) && launch_bonds(s->a, 0, st) != cudaSuccess) result = MD_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) result = MD_ERR_CUDA;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

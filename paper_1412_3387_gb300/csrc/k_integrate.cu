@@ -363,6 +363,43 @@ __global__ void k_bonds(KArgs a) {
       w[3] += 0.5 * d[1] * fy; w[4] += 0.5 * d[1] * fz; w[5] += 0.5 * d[2] * fz;
     }
   }
+  // harmonic angles this particle takes part in (as an end or the vertex):
+  // V = K/2 (theta - theta0)^2 with theta the angle at the vertex b between
+  // u = x_a - x_b and w = x_c - x_b; with c = cos theta, s = sin theta and
+  // g = K (theta - theta0) / s:
+  //   F_a = g (w / (|u| |w|) - c u / |u|^2), F_c likewise, F_b = -(F_a + F_c);
+  // each particle takes a third of V and of the virial u (x) F_a + w (x) F_c
+  for (int q = 0; q < a.max_angles; q++) {
+    const int32_t *e = a.atab + ((int64_t)ti * a.max_angles + q) * 3;
+    if (e[0] < 0) break;
+    any = true;
+    const double4 pa = ld_d4(a.pos + a.rtag[e[0]]);
+    const double4 pb = ld_d4(a.pos + a.rtag[e[1]]);
+    const double4 pc = ld_d4(a.pos + a.rtag[e[2]]);
+    double u[3], wv[3];
+    const double uu = exact_r2(pa, pb, rp, u);
+    const double ww = exact_r2(pc, pb, rp, wv);
+    const double ru = sqrt(uu), rw = sqrt(ww);
+    double cs = (u[0] * wv[0] + u[1] * wv[1] + u[2] * wv[2]) / (ru * rw);
+    cs = fmin(fmax(cs, -1.0), 1.0);
+    const double th = acos(cs);
+    const double sn = fmax(sqrt(1.0 - cs * cs), 1e-12);
+    const double g = a.angle_K * (th - a.angle_th0) / sn;
+    double fa[3], fc[3];
+    for (int k = 0; k < 3; k++) {
+      fa[k] = g * (wv[k] / (ru * rw) - cs * u[k] / uu);
+      fc[k] = g * (u[k] / (ru * rw) - cs * wv[k] / ww);
+    }
+    const int role = ti == e[0] ? 0 : ti == e[1] ? 1 : 2;
+    for (int k = 0; k < 3; k++)
+      f[k] += role == 0 ? fa[k] : role == 2 ? fc[k] : -(fa[k] + fc[k]);
+    if (ENERGY) {
+      pe += 0.5 * a.angle_K * (th - a.angle_th0) * (th - a.angle_th0) / 3.0;
+      w[0] += (u[0] * fa[0] + wv[0] * fc[0]) / 3.0; w[1] += (u[0] * fa[1] + wv[0] * fc[1]) / 3.0;
+      w[2] += (u[0] * fa[2] + wv[0] * fc[2]) / 3.0; w[3] += (u[1] * fa[1] + wv[1] * fc[1]) / 3.0;
+      w[4] += (u[1] * fa[2] + wv[1] * fc[2]) / 3.0; w[5] += (u[2] * fa[2] + wv[2] * fc[2]) / 3.0;
+    }
+  }
   if (!any) return;
   if (a.mixed) {
     float4 *F = reinterpret_cast<float4 *>(a.force) + i;

@@ -143,6 +143,7 @@ struct KArgs {
   int32_t *ident;      // [R] 1 while the replica's particles are in cell order
   int32_t *list_ok;    // [R] 1 while the replica's list matches its binning
   int32_t *btab;       // [N][max_bonds] partner tags (-1 = none)
+  int32_t *atab;       // [N][max_angles][3] angle triplets by tag (-1 = none)
   // sort scratch
   double4 *s_pos, *s_vel;
   int4 *s_img;
@@ -172,6 +173,8 @@ struct KArgs {
   double half_dt_m;    // dt / (2 m), computed once on the host
   double bond_K, bond_r0;
   int32_t bond_style;  // md_bond_style
+  int32_t max_angles;
+  double angle_K, angle_th0;
   // thermostat (md_set_integrator)
   int32_t integ;         // md_integrator
   double t_kT, t_c, t_sig, t_tau;  // kT; Langevin exp(-gamma dt), sqrt((1 - c^2) kT / m); NH tau

@@ -45,7 +45,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64), ("pair", _I32), ("n_types", _I32), ("pair_coeff", _P),
         ("precision", _I32), ("shift_energy", _I32), ("max_nb", _I32),
         ("sort_period", _I32), ("thermo_period", _I32), ("graph_steps", _I32),
-        ("max_bonds", _I32),
+        ("max_bonds", _I32), ("max_angles", _I32),
     ]
 
 
@@ -81,6 +81,7 @@ SIGNATURES = {
     "md_set_integrator": (C.c_int, [_P, _I32, _D, _D, C.c_uint64]),
     "md_set_newton": (C.c_int, [_P, _I32]),
     "md_set_bond_style": (C.c_int, [_P, _I32]),
+    "md_set_angles": (C.c_int, [_P, _P, _I64, _D, _D, _P]),
     "md_get_thermostat": (C.c_int, [_P, _P]),
 }
 INTEGRATORS = {"nve": 0, "langevin": 1, "nose-hoover": 2}
@@ -137,7 +138,8 @@ class MDSystem:
     def __init__(self, state, *, r_cut, r_skin, dt, pair="lj", coeff=((1.0, 1.0),),
                  precision="fp64", kT=1.0, seed=0, mass=1.0, shift_energy=False,
                  max_nb=None, sort_period=0, thermo_period=0, graph_steps=0,
-                 max_bonds=None, bond_K=0.0, bond_r0=0.0, device="cuda:0", stream=None):
+                 max_bonds=None, bond_K=0.0, bond_r0=0.0, max_angles=0, device="cuda:0",
+                 stream=None):
         import torch
         self.lib = load()
         self.device = torch.device(device)
@@ -185,6 +187,7 @@ class MDSystem:
         p.thermo_period = int(thermo_period)
         p.graph_steps = int(graph_steps)
         p.max_bonds = int(max_bonds)
+        p.max_angles = int(max_angles)
         self.params = p
         self.precision = precision
         size = _SZ()
@@ -271,6 +274,14 @@ class MDSystem:
         check(self.lib.md_reduce_thermo(self.handle, _ptr(out), _stream(stream)),
               "md_reduce_thermo")
         return out
+
+    def set_angles(self, angle_tags, K, theta0, stream=None):
+        """Harmonic angles over tag triplets (a, b, c), b the vertex; see
+        md_set_angles."""
+        t = np.ascontiguousarray(angle_tags, np.int32).reshape(-1, 3)
+        self._angles = t
+        check(self.lib.md_set_angles(self.handle, t.ctypes.data_as(C.c_void_p), t.shape[0],
+                                     float(K), float(theta0), _stream(stream)), "md_set_angles")
 
     def set_bond_style(self, style="harmonic"):
         """"harmonic" or "fene" (the r0 of set_bonds is then R0); see
