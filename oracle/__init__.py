@@ -71,6 +71,8 @@ def lib():
                 "orc_neighbors_cells": (I32, [I64, P, P, D, P, P, I32]),
                 "orc_lj_pair": (D, [D, D, D, P]),
                 "orc_pair_ncoeff": (I32, [I32]),
+                "orc_table_eval": (D, [D, P, I32, D, D, P]),
+                "orc_table_forces_brute": (None, [I64, P, P, P, D, I32, P, I32, D, P, P, P]),
                 "orc_pair_eval": (D, [I32, D, P, P]),
                 "orc_pair_forces_brute": (None, [I32, I64, P, P, P, D, I32, P, I32, P, P, P]),
                 "orc_pair_forces_nlist": (None, [I32, I64, P, P, P, D, I32, P, I32, P, P, I32, P, P, P]),
@@ -220,6 +222,31 @@ def lj_forces(pos, L, r_cut, coeff=((1.0, 1.0),), type=None, shift_energy=False,
         lib().orc_lj_forces_nlist(n, _p(pos), _p(t), _p(_box(L)), float(r_cut), ntypes,
                                   _p(c), int(shift_energy), _p(counts), _p(rows),
                                   rows.shape[1], _p(force), _p(virial), _p(absf))
+    return force, virial, absf
+
+
+def table_eval(r2, tab, r_min, r_cut):
+    """(F(r)/r, V) of a tabulated pair ([n_points][2] samples of V, F)."""
+    t = np.ascontiguousarray(tab, np.float64).reshape(-1, 2)
+    v = C.c_double()
+    fr = lib().orc_table_eval(float(r2), _p(t), t.shape[0], float(r_min), float(r_cut),
+                              C.byref(v))
+    return fr, v.value
+
+
+def table_forces(pos, L, r_cut, table, r_min, type=None):
+    """(force, virial, absf) of a tabulated pair potential, brute force;
+    table [ntypes][ntypes][n_points][2]."""
+    pos = _f64(pos)
+    n = pos.shape[0]
+    tab = np.ascontiguousarray(table, np.float64)
+    ntypes = tab.shape[0]
+    t = _i32(np.zeros(n) if type is None else type)
+    force = np.zeros((n, 4))
+    virial = np.zeros((n, 6))
+    absf = np.zeros(n)
+    lib().orc_table_forces_brute(n, _p(pos), _p(t), _p(_box(L)), float(r_cut), ntypes, _p(tab),
+                                 tab.shape[2], float(r_min), _p(force), _p(virial), _p(absf))
     return force, virial, absf
 
 

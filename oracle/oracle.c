@@ -308,6 +308,47 @@ void orc_pair_forces_nlist(int32_t kind, int64_t n, const double *pos, const int
     }
 }
 
+double orc_table_eval(double r2, const double *tab, int32_t n_points, double r_min,
+                      double r_cut, double *v) {
+    double r = sqrt(r2);
+    double dr = (r_cut - r_min) / (double)(n_points - 1);
+    double x = (r - r_min) / dr;
+    int32_t k = 0;
+    double t = 0.0;
+    if (x > 0.0) {
+        k = (int32_t)floor(x);
+        if (k > n_points - 2) k = n_points - 2;
+        t = x - (double)k;
+    }
+    const double *a = tab + 2 * k, *b = tab + 2 * (k + 1);
+    *v = a[0] + t * (b[0] - a[0]);
+    return (a[1] + t * (b[1] - a[1])) / r;
+}
+
+void orc_table_forces_brute(int64_t n, const double *pos, const int32_t *type,
+                            const double *L, double r_cut, int32_t ntypes,
+                            const double *table, int32_t n_points, double r_min,
+                            double *force, double *virial, double *absf) {
+    double rc2 = r_cut * r_cut;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++) {
+        pacc_t a;
+        pacc_clear(&a);
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double d[3];
+            double r2 = separation(pos + 4 * i, pos + 4 * j, L, d);
+            if (r2 < rc2) {
+                const double *tab = table + (size_t)2 * n_points * (size_t)(type[i] * ntypes + type[j]);
+                double v;
+                double fr = orc_table_eval(r2, tab, n_points, r_min, r_cut, &v);
+                pacc_pair(&a, d, fr, v);
+            }
+        }
+        pacc_store(&a, i, force, virial, absf);
+    }
+}
+
 void orc_lj_forces_brute(int64_t n, const double *pos, const int32_t *type,
                          const double *L, double r_cut, int32_t ntypes,
                          const double *coeff, int32_t shift_energy,

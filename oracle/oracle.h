@@ -103,6 +103,18 @@ void orc_pair_forces_nlist(int32_t kind, int64_t n, const double *pos, const int
                            int32_t max_nb, double *force, double *virial,
                            double *absf);
 
+/* Tabulated pair potential (Sec. 3 lists tabulated potentials): per ordered
+ * type pair, n_points samples (V_j, F_j) at r_j = r_min + j dr,
+ * dr = (r_cut - r_min) / (n_points - 1), F = -dV/dr; between samples V and
+ * F are interpolated linearly in r; below r_min they take their values at
+ * r_min.  table: [ntypes][ntypes][n_points][2].  Force factor F(r) / r. */
+double orc_table_eval(double r2, const double *tab, int32_t n_points, double r_min,
+                      double r_cut, double *v);
+void orc_table_forces_brute(int64_t n, const double *pos, const int32_t *type,
+                            const double *L, double r_cut, int32_t ntypes,
+                            const double *table, int32_t n_points, double r_min,
+                            double *force, double *virial, double *absf);
+
 /* Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11). */
 void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out);
 

@@ -216,6 +216,55 @@ def test_pair_forces_lj_kind_equals_lj_forces_and_rows_equal_brute():
     assert np.max(np.abs(fb[:, :3] - fn[:, :3])) <= 1e-13 * np.max(absf)
 
 
+# --------------------------------------------------------------------------
+# Tabulated pair potential (Sec. 3 lists tabulated potentials)
+
+def test_table_reproduces_linear_samples_and_converges_to_lj():
+    """Linear interpolation in r is exact for V and F that are linear in r
+    (any point, not only samples); below r_min the values at r_min hold; a
+    table sampled from LJ converges to LJ with the interpolation error
+    O(dr^2) (halving dr quarters it)."""
+    rmin, rc, n = 0.8, 2.5, 35
+    r = rmin + (rc - rmin) * np.arange(n) / (n - 1)
+    tab = np.stack([3.0 - 2.0 * r, 1.5 + 0.25 * r], axis=1)  # V, F = a + b r
+    for x in (0.8, 0.93, 1.37777, 2.2, 2.4999):
+        fr, v = oracle.table_eval(x * x, tab, rmin, rc)
+        assert v == pytest.approx(3.0 - 2.0 * x, rel=1e-14)
+        assert fr * x == pytest.approx(1.5 + 0.25 * x, rel=1e-14)
+    fr, v = oracle.table_eval(0.5 ** 2, tab, rmin, rc)
+    assert v == pytest.approx(3.0 - 2.0 * rmin) and fr * 0.5 == pytest.approx(1.5 + 0.25 * rmin)
+    errs = []
+    for n in (100, 200):
+        r = rmin + (rc - rmin) * np.arange(n) / (n - 1)
+        fv = [oracle.lj_pair(x * x) for x in r]
+        tab = np.array([[v, f * x] for (f, v), x in zip(fv, r)])
+        e = 0.0
+        for x in np.linspace(1.0, 2.4, 4001):
+            fr, v = oracle.table_eval(x * x, tab, rmin, rc)
+            f0, v0 = oracle.lj_pair(x * x)
+            e = max(e, abs(fr - f0) * x)
+        errs.append(e)
+    assert errs[1] == pytest.approx(errs[0] / 4, rel=0.1)
+
+
+def test_table_sums_on_the_lattice_equal_lj_sums():
+    """A fine table sampled from LJ gives the LJ per-site energies on the fcc
+    lattice to the interpolation error, and the lattice's symmetry leaves no
+    net force (the tabulated pair sums, type indexing and energy split)."""
+    rmin, rc = 0.5, 2.5
+    st = inputs.lj_fluid(4 * 6 ** 3, 0.8442, 1.0, seed=1)
+    L = st.box[0, 0]
+    n = 20001
+    r = rmin + (rc - rmin) * np.arange(n) / (n - 1)
+    fv = [oracle.lj_pair(x * x) for x in r]
+    tab = np.array([[[[v, f * x] for (f, v), x in zip(fv, r)]]])
+    f_t, vir_t, absf = oracle.table_forces(st.pos, L, rc, tab, rmin)
+    f_l, vir_l, _ = oracle.lj_forces(st.pos, L, rc)
+    # interpolation error at this resolution: ~ dr^2 |F''| / 8
+    assert np.allclose(f_t[:, 3], f_l[:, 3], rtol=1e-7, atol=1e-9)
+    assert np.max(np.abs(f_t[:, :3])) <= 1e-12 * np.max(absf)  # symmetric lattice
+
+
 def test_lj_multitype_coefficients_index_by_type_pair():
     st = inputs.lj_fluid(256, 0.8, 1.0, seed=4, jitter=0.1)
     L = st.box[0, 0]
