@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MD_ABI_VERSION 7
+#define MD_ABI_VERSION 8
 
 typedef struct md_system md_system;
 typedef struct CUstream_st *md_stream; /* a cudaStream_t; NULL = legacy default stream */
@@ -71,13 +71,17 @@ typedef enum { MD_FP64 = 0, MD_MIXED = 1 } md_precision;
  *   MD_PAIR_DPD     (A, gamma):         Groot-Warren, see md_params.kT / seed
  *   MD_PAIR_GAUSS   (eps, sigma):       V = eps exp(-r^2 / (2 sigma^2))
  *   MD_PAIR_MORSE   (D0, alpha, r0):    V = D0 [e^(-2 alpha (r - r0)) - 2 e^(-alpha (r - r0))]
- *   MD_PAIR_YUKAWA  (eps, kappa):       V = eps e^(-kappa r) / r */
+ *   MD_PAIR_YUKAWA  (eps, kappa):       V = eps e^(-kappa r) / r
+ *   MD_PAIR_TABLE   (no coefficients):  V and F = -dV/dr sampled per type pair
+ *                                       (md_set_pair_table), linear in r between
+ *                                       samples; zero until a table is set */
 typedef enum {
     MD_PAIR_LJ = 0,
     MD_PAIR_DPD = 1,
     MD_PAIR_GAUSS = 2,
     MD_PAIR_MORSE = 3,
-    MD_PAIR_YUKAWA = 4
+    MD_PAIR_YUKAWA = 4,
+    MD_PAIR_TABLE = 5
 } md_pair_kind;
 typedef enum { MD_KERNEL_NLIST = 0, MD_KERNEL_PAIR = 1 } md_kernel;
 typedef enum { MD_NVE = 0, MD_LANGEVIN = 1, MD_NOSE_HOOVER = 2 } md_integrator;
@@ -110,8 +114,9 @@ typedef struct {
     int32_t pair;                  /* md_pair_kind */
     int32_t n_types;               /* >= 1, <= 32 */
     const double *pair_coeff;      /* host [n_types][n_types][k], k = 3 for
-                                      Morse, else 2 (coefficients of
-                                      md_pair_kind, in its order); finite */
+                                      Morse, 0 for the table (may be NULL),
+                                      else 2 (coefficients of md_pair_kind, in
+                                      its order); finite */
     int32_t precision;             /* md_precision */
     int32_t shift_energy;          /* LJ, Gaussian, Morse, Yukawa: report
                                       V(r) - V(r_cut) as energy */
@@ -125,6 +130,7 @@ typedef struct {
     int32_t max_bonds;             /* bonds per particle capacity; 0 = no bonds */
     int32_t max_angles;            /* angles per particle capacity (as an end or the
                                       vertex); 0 = no angles */
+    int32_t table_points;          /* MD_PAIR_TABLE: samples per type pair, 2..65536 */
 } md_params;
 
 /* Thermodynamic row per replica, 8 doubles (Sec. 4.3.3 groups these global
@@ -166,6 +172,19 @@ md_status md_destroy_system(md_system *s);
  * max_bonds partners.  Synchronises `stream`. */
 md_status md_set_bonds(md_system *s, const int32_t *bond_tags, int64_t n_bonds,
                        double K, double r0, md_stream stream);
+
+/* Tabulated pair potential (Sec. 3 lists tabulated potentials), for a
+ * system created with pair = MD_PAIR_TABLE: table HOST double
+ * [n_types][n_types][table_points][2] = (V_j, F_j) at r_j = r_min + j dr,
+ * dr = (r_cut - r_min) / (table_points - 1), F = -dV/dr.  Between samples V and
+ * F are linear in r; below r_min they keep their values at r_min; the force
+ * on i is F(r) (x_i - x_j) / r for r < r_cut.  Energies are used as given
+ * (shift_energy does not apply).  Uploads the table (FP32 in mixed systems,
+ * FP64 otherwise) and synchronises `stream`.  Errors: MD_ERR_INVALID_ARG
+ * (another pair kind, 0 <= r_min < r_cut violated, non-finite samples),
+ * MD_ERR_CUDA. */
+md_status md_set_pair_table(md_system *s, const double *table, double r_min,
+                            md_stream stream);
 
 /* Harmonic angles V = K/2 (theta - theta0)^2 (Sec. 3 lists harmonic angle
  * potentials; Sec. 4.3.4 treats angles like bonds, as groups of particle

@@ -22,6 +22,7 @@ SOURCES = ["api.cu", "k_cells.cu", "k_nlist.cu", "k_pair.cu", "k_pair_lj_mixed.c
            "k_pair_lj_fp64.cu", "k_pair_dpd_mixed.cu", "k_pair_dpd_fp64.cu",
            "k_pair_gauss_mixed.cu", "k_pair_gauss_fp64.cu", "k_pair_morse_mixed.cu",
            "k_pair_morse_fp64.cu", "k_pair_yukawa_mixed.cu", "k_pair_yukawa_fp64.cu",
+           "k_pair_table_mixed.cu", "k_pair_table_fp64.cu",
            "k_integrate.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -97,13 +97,22 @@ struct Plan {
       o_brick_rep, o_brick_desc, o_cell_count, o_cell_start,
       o_chunk_sum, o_cell_idx, o_cellpos, o_pcell, o_pslot, o_n_nb, o_rtag, o_pos4f, o_oref, o_vel4f,
       o_nl, o_nl_tiles, o_force, o_virial, o_tpart, o_ds, o_rebuild, o_sort_now, o_last_sort, o_ident,
-      o_list_ok, o_coeff, o_btab, o_atab, o_s_pos, o_s_vel, o_s_img, o_s_tag, o_s_type, o_s_oref, o_nh,
+      o_list_ok, o_coeff, o_table, o_btab, o_atab, o_s_pos, o_s_vel, o_s_img, o_s_tag, o_s_type, o_s_oref, o_nh,
       o_nh_part;
   size_t total = 0;
 };
 
 // Coefficients per ordered type pair of each pair kind (md.h).
-int pair_ncoeff(int32_t pair) { return pair == MD_PAIR_MORSE ? 3 : 2; }
+int pair_ncoeff(int32_t pair) {
+  return pair == MD_PAIR_MORSE ? 3 : pair == MD_PAIR_TABLE ? 0 : 2;
+}
+
+// The float whose bits are those of the integer i (host side).
+float int_bits_as_float(int i) {
+  float f;
+  std::memcpy(&f, &i, sizeof(f));
+  return f;
+}
 
 md_status validate(const md_params *p) {
   if (!p) return MD_ERR_INVALID_ARG;
@@ -117,9 +126,12 @@ md_status validate(const md_params *p) {
     return MD_ERR_INVALID_ARG;
   if (!std::isfinite(p->r_cut) || !std::isfinite(p->r_skin) || !std::isfinite(p->dt))
     return MD_ERR_INVALID_ARG;
-  if (p->pair < MD_PAIR_LJ || p->pair > MD_PAIR_YUKAWA) return MD_ERR_INVALID_ARG;
+  if (p->pair < MD_PAIR_LJ || p->pair > MD_PAIR_TABLE) return MD_ERR_INVALID_ARG;
+  if (p->pair == MD_PAIR_TABLE && (p->table_points < 2 || p->table_points > 65536))
+    return MD_ERR_INVALID_ARG;
   if (p->precision != MD_FP64 && p->precision != MD_MIXED) return MD_ERR_INVALID_ARG;
-  if (p->n_types < 1 || p->n_types > kMaxTypes || !p->pair_coeff) return MD_ERR_INVALID_ARG;
+  if (p->n_types < 1 || p->n_types > kMaxTypes) return MD_ERR_INVALID_ARG;
+  if (pair_ncoeff(p->pair) > 0 && !p->pair_coeff) return MD_ERR_INVALID_ARG;
   if (p->pair == MD_PAIR_DPD && !(p->kT >= 0)) return MD_ERR_INVALID_ARG;
   for (int k = 0; k < pair_ncoeff(p->pair) * p->n_types * p->n_types; k++)
     if (!std::isfinite(p->pair_coeff[k])) return MD_ERR_INVALID_ARG;
@@ -279,6 +291,10 @@ md_status make_plan(const md_params *p, Plan &pl) {
   pl.o_ident = take(sizeof(int32_t) * R);
   pl.o_list_ok = take(sizeof(int32_t) * R);
   pl.o_coeff = take(64 * (size_t)p->n_types * p->n_types);
+  pl.o_table = take(p->pair == MD_PAIR_TABLE
+                        ? (p->precision == MD_MIXED ? 16 : 32) * (size_t)p->n_types * p->n_types *
+                              (size_t)p->table_points
+                        : 0);
   pl.o_btab = take(sizeof(int32_t) * (size_t)std::max(p->max_bonds, 0) * N);
   pl.o_atab = take(sizeof(int32_t) * 3 * (size_t)std::max(p->max_angles, 0) * N);
   pl.o_s_pos = take(sizeof(double4) * N);
@@ -428,7 +444,8 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   const int R = p->n_replicas;
   s->off.assign(p->replica_offset, p->replica_offset + R + 1);
   s->box.assign(p->box, p->box + 3 * R);
-  s->coeff.assign(p->pair_coeff, p->pair_coeff + pair_ncoeff(p->pair) * p->n_types * p->n_types);
+  if (pair_ncoeff(p->pair) > 0)
+    s->coeff.assign(p->pair_coeff, p->pair_coeff + pair_ncoeff(p->pair) * p->n_types * p->n_types);
   s->p.replica_offset = s->off.data();
   s->p.box = s->box.data();
   s->p.pair_coeff = s->coeff.data();
@@ -493,6 +510,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
   a.s_type = at<int32_t>(ws, pl.o_s_type);
   a.s_oref = at<float4>(ws, pl.o_s_oref);
   a.coeff = at<void>(ws, pl.o_coeff);
+  a.table = at<void>(ws, pl.o_table);
   a.nh = at<double>(ws, pl.o_nh);
   a.nh_part = at<double>(ws, pl.o_nh_part);
   a.integ = MD_NVE;
@@ -586,6 +604,7 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
     for (int tj = 0; tj < p->n_types; tj++) {
       const int c = ti * p->n_types + tj;
       const int nk = pair_ncoeff(p->pair);
+      if (nk == 0) continue;  // the table's coefficients come with md_set_pair_table
       const double c0 = p->pair_coeff[nk * c], c1 = p->pair_coeff[nk * c + 1];
       if (p->pair == MD_PAIR_GAUSS || p->pair == MD_PAIR_MORSE || p->pair == MD_PAIR_YUKAWA) {
         // Gaussian (eps, sigma), Morse (D0, alpha, r0), Yukawa (eps, kappa)
@@ -652,6 +671,11 @@ md_status md_create_system(const md_params *p, const md_particles *parts, void *
       cudaMemcpyAsync(at<void>(ws, pl.o_brick_rep), brep.data(), sizeof(int32_t) * brep.size(), cudaMemcpyHostToDevice, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_brick_desc), 0, sizeof(BrickDesc) * (size_t)pl.n_bricks, stream) ||
       cudaMemcpyAsync(at<void>(ws, pl.o_coeff), coeff.data(), coeff.size(), cudaMemcpyHostToDevice, stream) ||
+      cudaMemsetAsync(at<void>(ws, pl.o_table), 0,
+                      p->pair == MD_PAIR_TABLE
+                          ? (mixed ? 16 : 32) * (size_t)p->n_types * p->n_types * (size_t)p->table_points
+                          : 0,
+                      stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_cell_count), 0, sizeof(int32_t) * pl.n_cells, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_cell_start), 0, sizeof(int32_t) * pl.n_cells, stream) ||
       cudaMemsetAsync(at<void>(ws, pl.o_n_nb), 0, sizeof(int32_t) * pl.n_pad, stream) ||
@@ -725,6 +749,57 @@ md_status md_set_bonds(md_system *s, const int32_t *bond_tags, int64_t n_bonds, 
   s->a.bond_r0 = r0;
   s->gvalid = false;
   s->built = false;  // forces must include the bonds before the next step
+  return MD_OK;
+}
+
+md_status md_set_pair_table(md_system *s, const double *table, double r_min, md_stream stream_) {
+  if (!s || !table || s->p.pair != MD_PAIR_TABLE) return MD_ERR_INVALID_ARG;
+  const double rc = s->p.r_cut;
+  if (!(r_min >= 0) || !(r_min < rc)) return MD_ERR_INVALID_ARG;
+  const int nt = s->p.n_types, np = s->p.table_points;
+  const size_t npairs = (size_t)nt * nt;
+  for (size_t k = 0; k < npairs * np * 2; k++)
+    if (!std::isfinite(table[k])) return MD_ERR_INVALID_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  const bool mixed = s->p.precision == MD_MIXED;
+  const double inv_dr = (double)(np - 1) / (rc - r_min);
+  // segments (V_j, F_j, V_j+1 - V_j, F_j+1 - F_j), j = 0 .. np - 2, per
+  // ordered type pair at np * pair; the last slot of a pair is unused
+  std::vector<double> seg(npairs * np * 4, 0.0);
+  std::vector<unsigned char> coeff(64 * npairs, 0);
+  for (size_t c = 0; c < npairs; c++) {
+    const double *t = table + c * np * 2;
+    for (int j = 0; j + 1 < np; j++) {
+      double *g = seg.data() + (c * np + j) * 4;
+      g[0] = t[2 * j], g[1] = t[2 * j + 1];
+      g[2] = t[2 * j + 2] - t[2 * j], g[3] = t[2 * j + 3] - t[2 * j + 1];
+    }
+    const int first = (int)(c * np);
+    if (mixed) {
+      PotCoeffF f{(float)r_min, (float)inv_dr, (float)(np - 2), int_bits_as_float(first), 0, 0, 0, 0};
+      std::memcpy(coeff.data() + sizeof(PotCoeffF) * c, &f, sizeof(f));
+      if (c == 0) s->a.pot1f = f;
+    } else {
+      PotCoeffD d{r_min, inv_dr, (double)(np - 2), (double)first, 0, 0, 0, 0};
+      std::memcpy(coeff.data() + sizeof(PotCoeffD) * c, &d, sizeof(d));
+    }
+  }
+  if (mixed) {
+    std::vector<float> f(seg.size());
+    for (size_t k = 0; k < seg.size(); k++) f[k] = (float)seg[k];
+    MD_CUDA(cudaMemcpyAsync(const_cast<void *>(s->a.table), f.data(), sizeof(float) * f.size(),
+                            cudaMemcpyHostToDevice, stream));
+    MD_CUDA(cudaMemcpyAsync(const_cast<void *>(s->a.coeff), coeff.data(), sizeof(PotCoeffF) * npairs,
+                            cudaMemcpyHostToDevice, stream));
+  } else {
+    MD_CUDA(cudaMemcpyAsync(const_cast<void *>(s->a.table), seg.data(), sizeof(double) * seg.size(),
+                            cudaMemcpyHostToDevice, stream));
+    MD_CUDA(cudaMemcpyAsync(const_cast<void *>(s->a.coeff), coeff.data(), sizeof(PotCoeffD) * npairs,
+                            cudaMemcpyHostToDevice, stream));
+  }
+  MD_CUDA(cudaStreamSynchronize(stream));
+  s->gvalid = false;
+  s->built = false;  // forces of the new table before the next step
   return MD_OK;
 }
 

@@ -4,7 +4,7 @@
 
 namespace mdgb {
 
-constexpr int kLJ = 0, kDPD = 1, kGauss = 2, kMorse = 3, kYukawa = 4;
+constexpr int kLJ = 0, kDPD = 1, kGauss = 2, kMorse = 3, kYukawa = 4, kTable = 5;
 
 template <int POT, bool MIXED>
 cudaError_t launch_pair_form(const KArgs &a, Launch l, int want_virial, cudaStream_t st);
@@ -25,6 +25,7 @@ void pair_init_attributes() {
   form_attributes<kGauss>();
   form_attributes<kMorse>();
   form_attributes<kYukawa>();
+  form_attributes<kTable>();
 }
 
 template <int POT>
@@ -48,6 +49,7 @@ cudaError_t launch_pair(const KArgs &a, Launch l, int want_virial, cudaStream_t 
     case kGauss: return launch_pot<kGauss>(a, l, want_virial, st);
     case kMorse: return launch_pot<kMorse>(a, l, want_virial, st);
     case kYukawa: return launch_pot<kYukawa>(a, l, want_virial, st);
+    case kTable: return launch_pot<kTable>(a, l, want_virial, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -65,6 +67,7 @@ int max_block_pair(const KArgs &a, int w, int want_virial) {
     case kGauss: return max_block_pot<kGauss>(a, w, want_virial);
     case kMorse: return max_block_pot<kMorse>(a, w, want_virial);
     case kYukawa: return max_block_pot<kYukawa>(a, w, want_virial);
+    case kTable: return max_block_pot<kTable>(a, w, want_virial);
     default: return 0;
   }
 }

@@ -91,7 +91,9 @@ struct DPDCoeffD { double A, gamma, sigma_rdt, pad; };  // sigma / sqrt(dt)
 struct DPDCoeffF { float A, gamma, sigma_rdt, pad; };
 // Gaussian (c0 = 1 / (2 sigma^2), c1 = eps / sigma^2, c2 = eps), Morse
 // (c0 = alpha, c1 = r0, c2 = 2 D0 alpha, c3 = D0), Yukawa (c0 = kappa,
-// c1 = eps); vshift = V(r_cut) when energies are shifted.
+// c1 = eps); vshift = V(r_cut) when energies are shifted.  Table: c0 = r_min,
+// c1 = 1 / dr, c2 = the last segment's index, c3 = the type pair's first
+// segment (integer bits); each segment is (V_j, F_j, V_j+1 - V_j, F_j+1 - F_j).
 struct PotCoeffD { double c0, c1, c2, c3, vshift, pad0, pad1, pad2; };  // 64 B
 struct PotCoeffF { float c0, c1, c2, c3, vshift, pad0, pad1, pad2; };
 
@@ -150,6 +152,7 @@ struct KArgs {
   int32_t *s_tag, *s_type;
   float4 *s_oref;
   const void *coeff;   // LJCoeff* / DPDCoeff* / PotCoeff* [ntypes^2], precision-matched
+  const void *table;   // float4* / double4* segments of tabulated pairs
   // the single type pair's FP32 coefficients, as kernel parameters: the
   // mixed pair loops take them as constant operands instead of re-loading
   // them from memory

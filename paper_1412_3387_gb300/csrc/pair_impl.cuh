@@ -29,7 +29,7 @@
 
 namespace mdgb {
 
-constexpr int kLJ = 0, kDPD = 1, kGauss = 2, kMorse = 3, kYukawa = 4;
+constexpr int kLJ = 0, kDPD = 1, kGauss = 2, kMorse = 3, kYukawa = 4, kTable = 5;
 
 namespace {
 constexpr unsigned FULL = 0xffffffffu;
@@ -69,6 +69,32 @@ __device__ __forceinline__ double seg_sum(double v) {
 #pragma unroll
   for (int m = W / 2; m >= 1; m >>= 1) v += __shfl_xor_sync(FULL, v, m);
   return v;
+}
+
+// Tabulated pair: V and F = -dV/dr linear in r between samples at r_min + j
+// dr, held at their r_min values below r_min; segment j = (V_j, F_j,
+// V_j+1 - V_j, F_j+1 - F_j).  Returns F / r, V in v.  (A non-finite r^2, the
+// sentinel, lands in segment 0; its result is never used.)
+__device__ __forceinline__ float table_fr(const PotCoeffF &c, const float4 *tab, float r2,
+                                          float &v) {
+  const float rinv = rsqrtf(r2), r = r2 * rinv;
+  const float x = fmaxf((r - c.c0) * c.c1, 0.f);
+  const int k = min((int)x, (int)c.c2);
+  const float t = x - (float)k;
+  const float4 s = __ldg(tab + __float_as_int(c.c3) + k);
+  v = fmaf(t, s.z, s.x);
+  return fmaf(t, s.w, s.y) * rinv;
+}
+
+__device__ __forceinline__ double table_fr(const PotCoeffD &c, const double4 *tab, double r2,
+                                           double &v) {
+  const double r = sqrt(r2);
+  const double x = fmax((r - c.c0) * c.c1, 0.0);
+  const int k = min((int)x, (int)c.c2);
+  const double t = x - (double)k;
+  const double4 s = ld_d4(tab + (int64_t)c.c3 + k);
+  v = s.x + t * s.z;
+  return (s.y + t * s.w) / r;
 }
 
 // Gaussian V = eps e^(-r^2 / 2 sigma^2), Morse V = D0 (x^2 - 2 x) with
@@ -148,6 +174,11 @@ struct MixedPair {
       const float r6 = r2i * r2i * r2i;
       fr = r2i * r6 * (c.lj1 * r6 - c.lj2);
       if (ENERGY) v = r6 * (c.lj3 * r6 - c.lj4) - c.vshift;
+    } else if (POT == kTable) {
+      const PotCoeffF c = ONE ? pc0 : reinterpret_cast<const PotCoeffF *>(a.coeff)[cidx];
+      float vv;
+      fr = table_fr(c, reinterpret_cast<const float4 *>(a.table), r2, vv);
+      if (ENERGY) v = vv;
     } else if (POT != kDPD) {
       const PotCoeffF c = ONE ? pc0 : reinterpret_cast<const PotCoeffF *>(a.coeff)[cidx];
       float vv;
@@ -211,6 +242,11 @@ struct DoublePair {
       const double r6 = r2i * r2i * r2i;
       fr = r2i * r6 * (c.lj1 * r6 - c.lj2);
       if (ENERGY) v = r6 * (c.lj3 * r6 - c.lj4) - c.vshift;
+    } else if (POT == kTable) {
+      const PotCoeffD c = ONE ? pd0 : reinterpret_cast<const PotCoeffD *>(a.coeff)[cidx];
+      double vv;
+      fr = table_fr(c, reinterpret_cast<const double4 *>(a.table), r2d, vv);
+      if (ENERGY) v = vv;
     } else if (POT != kDPD) {
       const PotCoeffD c = ONE ? pd0 : reinterpret_cast<const PotCoeffD *>(a.coeff)[cidx];
       double vv;
@@ -401,6 +437,7 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
   const LJCoeffF lj = a.lj1f;
   const DPDCoeffF dc = a.dpd1f;
   const PotCoeffF pc = a.pot1f;
+  const float4 *table = reinterpret_cast<const float4 *>(a.table);
   const int ntypes = a.ntypes, ti = cell_type(__float_as_uint(oi.w));
   const void *coeff = a.coeff;
   const float inv_rc = (float)(1.0 / a.r_cut), r_cut_f = (float)a.r_cut;
@@ -433,7 +470,7 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
                                 : reinterpret_cast<const PotCoeffF *>(coeff)[
                                       ti * ntypes + cell_type(__float_as_uint(ojw))];
         float vv;
-        const float f = pot_fr<POT>(c, r2, vv);
+        const float f = POT == kTable ? table_fr(c, table, r2, vv) : pot_fr<POT>(c, r2, vv);
         fr = in ? f : 0.f;
         if (ENERGY) en = in ? vv - c.vshift : 0.f;
       } else {

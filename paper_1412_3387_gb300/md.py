@@ -23,10 +23,10 @@ STATUS = {
     7: "MD_ERR_CELL_OVERFLOW", 8: "MD_ERR_STATE", 9: "MD_ERR_TIMEOUT",
 }
 FP64, MIXED = 0, 1
-LJ, DPD, GAUSS, MORSE, YUKAWA = 0, 1, 2, 3, 4
+LJ, DPD, GAUSS, MORSE, YUKAWA, TABLE = 0, 1, 2, 3, 4, 5
 # pair kinds by name, and their coefficients per ordered type pair (md.h)
-PAIRS = {"lj": LJ, "dpd": DPD, "gauss": GAUSS, "morse": MORSE, "yukawa": YUKAWA}
-PAIR_NCOEFF = {LJ: 2, DPD: 2, GAUSS: 2, MORSE: 3, YUKAWA: 2}
+PAIRS = {"lj": LJ, "dpd": DPD, "gauss": GAUSS, "morse": MORSE, "yukawa": YUKAWA, "table": TABLE}
+PAIR_NCOEFF = {LJ: 2, DPD: 2, GAUSS: 2, MORSE: 3, YUKAWA: 2, TABLE: 0}
 KERNEL_NLIST, KERNEL_PAIR = 0, 1
 THERMO_FIELDS = ("ke", "pe", "virial", "pressure", "temperature", "px", "py", "pz")
 
@@ -45,7 +45,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64), ("pair", _I32), ("n_types", _I32), ("pair_coeff", _P),
         ("precision", _I32), ("shift_energy", _I32), ("max_nb", _I32),
         ("sort_period", _I32), ("thermo_period", _I32), ("graph_steps", _I32),
-        ("max_bonds", _I32), ("max_angles", _I32),
+        ("max_bonds", _I32), ("max_angles", _I32), ("table_points", _I32),
     ]
 
 
@@ -81,6 +81,7 @@ SIGNATURES = {
     "md_set_integrator": (C.c_int, [_P, _I32, _D, _D, C.c_uint64]),
     "md_set_newton": (C.c_int, [_P, _I32]),
     "md_set_bond_style": (C.c_int, [_P, _I32]),
+    "md_set_pair_table": (C.c_int, [_P, _P, _D, _P]),
     "md_set_angles": (C.c_int, [_P, _P, _I64, _D, _D, _P]),
     "md_get_thermostat": (C.c_int, [_P, _P]),
 }
@@ -138,8 +139,8 @@ class MDSystem:
     def __init__(self, state, *, r_cut, r_skin, dt, pair="lj", coeff=((1.0, 1.0),),
                  precision="fp64", kT=1.0, seed=0, mass=1.0, shift_energy=False,
                  max_nb=None, sort_period=0, thermo_period=0, graph_steps=0,
-                 max_bonds=None, bond_K=0.0, bond_r0=0.0, max_angles=0, device="cuda:0",
-                 stream=None):
+                 max_bonds=None, bond_K=0.0, bond_r0=0.0, max_angles=0, table_points=0,
+                 n_types=None, device="cuda:0", stream=None):
         import torch
         self.lib = load()
         self.device = torch.device(device)
@@ -154,10 +155,14 @@ class MDSystem:
         if pair not in PAIRS:
             raise ValueError(f"unknown pair kind {pair!r}")
         nk = PAIR_NCOEFF[PAIRS[pair]]
-        coeff = np.ascontiguousarray(coeff, np.float64)
-        n_types = int(round(np.sqrt(coeff.size / nk)))
-        if n_types * n_types * nk != coeff.size:
-            raise ValueError(f"{pair} needs {nk} coefficients per ordered type pair")
+        if nk == 0:  # tabulated: the table comes with set_pair_table
+            n_types = int(n_types or (int(np.max(state.type)) + 1 if state.n else 1))
+            coeff = np.zeros((n_types, n_types, 0))
+        else:
+            coeff = np.ascontiguousarray(coeff, np.float64)
+            n_types = int(round(np.sqrt(coeff.size / nk)))
+            if n_types * n_types * nk != coeff.size:
+                raise ValueError(f"{pair} needs {nk} coefficients per ordered type pair")
         self._off = np.ascontiguousarray(state.offsets, np.int64)
         self._box = np.ascontiguousarray(state.box, np.float64).reshape(-1, 3)
         self._coeff = coeff.reshape(n_types, n_types, nk).copy()
@@ -179,7 +184,8 @@ class MDSystem:
         p.seed = int(seed)
         p.pair = PAIRS[pair]
         p.n_types = n_types
-        p.pair_coeff = self._coeff.ctypes.data
+        p.pair_coeff = self._coeff.ctypes.data if nk else None
+        p.table_points = int(table_points)
         p.precision = FP64 if precision == "fp64" else MIXED
         p.shift_energy = int(bool(shift_energy))
         p.max_nb = int(max_nb)
@@ -282,6 +288,14 @@ class MDSystem:
         self._angles = t
         check(self.lib.md_set_angles(self.handle, t.ctypes.data_as(C.c_void_p), t.shape[0],
                                      float(K), float(theta0), _stream(stream)), "md_set_angles")
+
+    def set_pair_table(self, table, r_min, stream=None):
+        """Tabulated pair (pair="table"): table [n_types][n_types][points][2]
+        samples (V, F) from r_min to r_cut; see md_set_pair_table."""
+        t = np.ascontiguousarray(table, np.float64)
+        self._table = t
+        check(self.lib.md_set_pair_table(self.handle, t.ctypes.data_as(C.c_void_p), float(r_min),
+                                         _stream(stream)), "md_set_pair_table")
 
     def set_bond_style(self, style="harmonic"):
         """"harmonic" or "fene" (the r0 of set_bonds is then R0); see

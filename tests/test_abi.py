@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version_and_status_strings(lib):
-    assert lib.md_abi_version() == 7
+    assert lib.md_abi_version() == 8
     for code in range(11):
         assert lib.md_status_string(code)
 

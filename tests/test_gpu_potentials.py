@@ -141,3 +141,59 @@ def test_bad_coefficients_are_refused():
     with pytest.raises(Exception):
         md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, pair="yukawa",
                     coeff=[[1.0, float("nan")]])
+
+
+def lj_table(n_points, r_min, r_cut, eps=1.0, sigma=1.0):
+    """(V, F) samples of LJ on the table grid (the table's input)."""
+    r = r_min + (r_cut - r_min) * np.arange(n_points) / (n_points - 1)
+    out = np.zeros((n_points, 2))
+    for j, x in enumerate(r):
+        fr, v = oracle.lj_pair(x * x, eps, sigma)
+        out[j] = (v, fr * x)
+    return out
+
+
+@pytest.mark.parametrize("prec", ("fp64", "mixed"))
+def test_tabulated_pair_matches_oracle(prec):
+    """A tabulated pair (Sec. 3) with two types: the GPU interpolates the same
+    samples as the oracle (forces, energies, virials; the 1e-12 rule for FP64,
+    the mixed tolerance for FP32)."""
+    st = liquid()
+    st.type = (np.arange(st.n) % 4 == 0).astype(np.int32)
+    L = st.box[0]
+    n_points, r_min = 1201, 0.6
+    tab = np.zeros((2, 2, n_points, 2))
+    for a, b, eps in ((0, 0, 1.0), (0, 1, 0.8), (1, 0, 0.8), (1, 1, 1.3)):
+        tab[a, b] = lj_table(n_points, r_min, 2.5, eps=eps)
+    ref, vref, absf = oracle.table_forces(st.pos, L, 2.5, tab, r_min, type=st.type)
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, pair="table", table_points=n_points,
+                    n_types=2, precision=prec)
+    s.set_pair_table(tab, r_min)
+    s.set_tuning(md.KERNEL_PAIR, 128, 2)
+    s.prepare()
+    s.compute_pair(want_virial=True)
+    f, v = (x.cpu().numpy() for x in s.forces(virial=True))
+    s.check_error()
+    if prec == "fp64":
+        fp64_force_check(f, ref, absf, "table")
+        assert np.allclose(f[:, 3], ref[:, 3], rtol=1e-12, atol=1e-12 * absf.max())
+        assert np.allclose(v, vref, rtol=1e-11, atol=1e-12 * absf.max())
+    else:
+        rms, mx = mixed_force_stats(f, ref, absf)
+        assert rms <= 1e-5 and mx <= 1e-3, (rms, mx)
+    # a run on the table stays close to LJ's own energy scale and reports no error
+    s.run(20)
+    s.check_error()
+
+
+def test_table_arguments_are_checked():
+    st = liquid(n=2000)
+    with pytest.raises(md.MDError):  # no sample count
+        md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, pair="table", n_types=1)
+    s = md.MDSystem(st, r_cut=2.5, r_skin=0.3, dt=0.005, pair="table", table_points=10,
+                    n_types=1)
+    with pytest.raises(md.MDError):
+        s.set_pair_table(np.zeros((1, 1, 10, 2)), 2.6)  # r_min beyond r_cut
+    with pytest.raises(md.MDError):
+        s.set_pair_table(np.full((1, 1, 10, 2), np.nan), 0.5)
+    s.set_pair_table(np.zeros((1, 1, 10, 2)), 0.5)
