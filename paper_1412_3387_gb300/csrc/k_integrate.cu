@@ -111,7 +111,11 @@ __device__ __forceinline__ void langevin_theta(int32_t tag, uint64_t step, uint6
 // the same velocity-Verlet step written as one kick.
 // Grid-stride: a bounded grid keeps the end-of-kernel ticket (one fenced
 // atomic per block) cheap.
-__global__ void __launch_bounds__(256) k_integrate1(KArgs a, double hk) {
+// One instance per integrator (INTEG = md_integrator), so the plain
+// velocity-Verlet form carries no thermostat registers: at most 64 registers
+// (4 blocks of 256 threads per SM) keep enough loads in flight.
+template <int INTEG>
+__global__ void __launch_bounds__(256, 4) k_integrate1(KArgs a, double hk) {
   __shared__ int is_last;
   const int64_t t = a.ds->step;
   const int par = (int)((t + 1) & 1);
@@ -124,7 +128,7 @@ __global__ void __launch_bounds__(256) k_integrate1(KArgs a, double hk) {
     const double3 f = ld_force3(a, i);
     int4 img = a.image[i];
     const int4 img0 = img;
-    if (a.integ == MD_NOSE_HOOVER) {
+    if (INTEG == MD_NOSE_HOOVER) {
       // the thermostat's half steps at the end of the previous step and at
       // the start of this one, in that order
       const double s1 = a.nh[kNhFields * r + 3], s2 = a.nh[kNhFields * r + 2];
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(256) k_integrate1(KArgs a, double hk) {
       v.y = (v.y * s1) * s2;
       v.z = (v.z * s1) * s2;
     }
-    if (a.integ == MD_LANGEVIN) {
+    if (INTEG == MD_LANGEVIN) {
       double th[3];
       langevin_theta(a.tag[i], (uint64_t)(t + 1), a.t_seed, th);
       const double hdt = 0.5 * a.dt;
@@ -605,11 +609,14 @@ __global__ void k_philox(const uint32_t *in, uint32_t *out, int64_t n) {
 }  // namespace
 
 cudaError_t launch_integrate1(const KArgs &a, cudaStream_t st, bool fold_kick) {
-  // the step counter must advance even for an empty system; at most 8
+  // the step counter must advance even for an empty system; one wave of 4
   // blocks per SM (152 SMs), grid-stride beyond that
   const unsigned need = blocks_for(a.n > 0 ? a.n : 1, 256);
-  k_integrate1<<<need < 152u * 8u ? need : 152u * 8u, 256, 0, st>>>(
-      a, fold_kick ? 2.0 * a.half_dt_m : a.half_dt_m);
+  const unsigned grid = need < 152u * 4u ? need : 152u * 4u;
+  const double hk = fold_kick ? 2.0 * a.half_dt_m : a.half_dt_m;
+  if (a.integ == MD_LANGEVIN) k_integrate1<MD_LANGEVIN><<<grid, 256, 0, st>>>(a, hk);
+  else if (a.integ == MD_NOSE_HOOVER) k_integrate1<MD_NOSE_HOOVER><<<grid, 256, 0, st>>>(a, hk);
+  else k_integrate1<MD_NVE><<<grid, 256, 0, st>>>(a, hk);
   return cudaGetLastError();
 }
 
