@@ -109,6 +109,12 @@ __device__ __forceinline__ void langevin_theta(int32_t tag, uint64_t step, uint6
 // hk = dt / (2m); or dt / m when the previous step's second half-kick was
 // left out (inside a run): v(t - 1/2) -> v(t + 1/2) = v(t - 1/2) + dt F(t) / m,
 // the same velocity-Verlet step written as one kick.
+// The FP32 velocity copy of mixed-precision DPD.  Out of line, so that other
+// systems do not issue its conversions under a predicate.
+static __device__ __noinline__ void store_vel4f(const KArgs &a, int64_t p, const double4 &v, int64_t i) {
+  a.vel4f[p] = make_float4((float)v.x, (float)v.y, (float)v.z, __int_as_float(a.tag[i]));
+}
+
 // Grid-stride: a bounded grid keeps the end-of-kernel ticket (one fenced
 // atomic per block) cheap.
 // One instance per integrator (INTEG = md_integrator), so the plain
@@ -171,7 +177,7 @@ __global__ void __launch_bounds__(256, 4) k_integrate1(KArgs a, double hk) {
         outside_box(x.z, __double_as_longlong(rp.L[2]))) {
       if (atomicOr(&a.ds->error, kErrNonfinite) == 0u) a.ds->error_detail = i;
     }
-    if (a.vel4f) a.vel4f[p] = make_float4((float)v.x, (float)v.y, (float)v.z, __int_as_float(a.tag[i]));
+    if (a.vel4f) store_vel4f(a, p, v, i);
   }
   // Block barrier, then one fence + ticket per block (release of every
   // thread's flag store through the barrier).

@@ -227,10 +227,17 @@ __device__ __forceinline__ int cell_coord(double x, double inv_h, int nc) {
 // (a few per clock per SM), so the centre comes from a table and the periodic
 // fold (needed only once the particle has crossed the box since its frame
 // was set) is decided on the FP32 value: offsets stay below h + skin << L/2.
+// The periodic image of the offset (a particle that crossed the box since its
+// frame cell was chosen).  Out of line: the FP64 work stays off the common
+// path instead of being issued there under a predicate.
+static __device__ __noinline__ float frame_offset_image(double d, double L, float cq, float o) {
+  return (float)(d + (o > 0.f ? -L : L)) - cq;
+}
+
 __device__ __forceinline__ float frame_offset(double x, double ctr_q, float cq, float Lf, double L) {
   const double d = x - ctr_q;
   const float o = (float)d - cq;
-  if (fabsf(o) > 0.5f * Lf) return (float)(d + (o > 0.f ? -L : L)) - cq;
+  if (fabsf(o) > 0.5f * Lf) return frame_offset_image(d, L, cq, o);
   return o;
 }
 
