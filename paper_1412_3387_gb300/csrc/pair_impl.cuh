@@ -71,6 +71,13 @@ __device__ __forceinline__ double seg_sum(double v) {
   return v;
 }
 
+// FP32 uniform on (0, 1) from a 32-bit random word: ((w >> 9) + 1/2) 2^-23,
+// built from the bits (1 + (w >> 9) 2^-23 is the float with those mantissa
+// bits; subtracting 1 - 2^-24 is exact), with no integer-to-float conversion.
+__device__ __forceinline__ float unit_uniform(uint32_t w) {
+  return __uint_as_float(0x3f800000u | (w >> 9)) - 0.99999994039535522f;
+}
+
 // Tabulated pair: V and F = -dV/dr linear in r between samples at r_min + j
 // dr, held at their r_min values below r_min; segment j = (V_j, F_j,
 // V_j+1 - V_j, F_j+1 - F_j).  Returns F / r, V in v.  (A non-finite r^2, the
@@ -192,7 +199,7 @@ struct MixedPair {
       const float w = 1.f - rr * inv_rc;
       const float dot = dx * (vi4.x - vj.x) + dy * (vi4.y - vj.y) + dz * (vi4.z - vj.z);
       const uint32_t word = dpd_word(tag_i, __float_as_int(vj.w), step, a.seed);
-      const float uu = ((float)(word >> 8) + 0.5f) * 5.9604644775390625e-08f;  // 2^-24
+      const float uu = unit_uniform(word);
       const float theta = 1.7320508075688772f * (2.f * uu - 1.f);
       const float fmag = c.A * w - c.gamma * w * w * dot * rinv + c.sigma_rdt * w * theta;
       fr = fmag * rinv;
@@ -482,7 +489,7 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
         const float wgt = fmaf(-r2 * rinv, inv_rc, 1.f);
         const float dot = dx * (vi4.x - vj.x) + dy * (vi4.y - vj.y) + dz * (vi4.z - vj.z);
         const uint32_t word = dpd_word(tag_i, __float_as_int(vj.w), step, seed);
-        const float uu = ((float)(word >> 8) + 0.5f) * 5.9604644775390625e-08f;  // 2^-24
+        const float uu = unit_uniform(word);
         const float theta = 1.7320508075688772f * (2.f * uu - 1.f);
         const float fmag = c.A * wgt - c.gamma * wgt * wgt * dot * rinv + c.sigma_rdt * wgt * theta;
         fr = in ? fmag * rinv : 0.f;
