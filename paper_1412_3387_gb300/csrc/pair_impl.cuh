@@ -300,14 +300,6 @@ struct DoublePair {
 
 // V consecutive 16-bit row entries of one lane, loaded with one instruction.
 template <int V> struct RowWord;
-
-// A row word from lane `src` of this lane's segment of `width` lanes.
-__device__ __forceinline__ uint2 shfl_row(const uint2 &w, int src, int width) {
-  return make_uint2(__shfl_sync(0xffffffffu, w.x, src, width), __shfl_sync(0xffffffffu, w.y, src, width));
-}
-__device__ __forceinline__ uint32_t shfl_row(uint32_t w, int src, int width) {
-  return __shfl_sync(0xffffffffu, w, src, width);
-}
 template <> struct RowWord<4> {
   using T = uint2;
   static __device__ __forceinline__ T load(const uint16_t *p) {
@@ -514,74 +506,6 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
       }
     }
   };
-  // DPD, mixed precision: an entry's cost is mostly its Philox draw, and about
-  // half of a list's entries lie beyond r_cut.  So the block's in-range
-  // entries (r^2 below the band) are first counted, then shared out among the
-  // W lanes of their particle: in round k, lane sl takes the particle's
-  // in-range entry k W + sl (lanes in order, each lane's entries in order).
-  // Rounds run to the warp's largest count; every lane of a particle adds to
-  // that particle's sums, so no result moves back.
-  auto shfl_word = [&](const Word &w, int src) { return shfl_row(w, src, W); };
-  auto dpd_block = [&](const Word &w, float &gx, float &gy, float &gz, float &bmin) {
-    unsigned m = 0u;
-#pragma unroll
-    for (int v = 0; v < V; v++) {
-      float dx, dy, dz, ojw;
-      sep(RW::get(w, v), dx, dy, dz, ojw);
-      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-      bmin = fminf(bmin, fabsf(r2 - rc2f));
-      m |= (r2 < lo ? 1u : 0u) << v;
-    }
-    const int cnt = __popc(m);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < W; o <<= 1) {
-      const int t = __shfl_up_sync(FULL, incl, o, W);
-      if (sl >= o) incl += t;
-    }
-    const int excl = incl - cnt;
-    const int tot = __shfl_sync(FULL, incl, W - 1, W);
-    const int rounds = (int)__reduce_max_sync(FULL, (unsigned)((tot + W - 1) / W));
-    for (int k = 0; k < rounds; k++) {
-      const int idx = k * W + sl;
-      // the lane holding item idx: the last lane whose exclusive count is
-      // <= idx (the counts never decrease along the lanes)
-      int s = 0;
-#pragma unroll
-      for (int o = W / 2; o >= 1; o >>= 1)
-        if (__shfl_sync(FULL, excl, s + o, W) <= idx) s += o;
-      unsigned ms = __shfl_sync(FULL, m, s, W);
-      const int j = idx - __shfl_sync(FULL, excl, s, W);
-      const Word ws = shfl_word(w, s);
-      if (idx < tot) {
-        for (int q = 0; q < j; q++) ms &= ms - 1u;  // drop the j lower in-range entries
-        const uint32_t e = RW::get(ws, __ffs(ms) - 1);
-        float dx, dy, dz, ojw;
-        sep(e, dx, dy, dz, ojw);
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const DPDCoeffF c = ONE ? dc
-                                : reinterpret_cast<const DPDCoeffF *>(coeff)[
-                                      ti * ntypes + cell_type(__float_as_uint(ojw))];
-        const float4 vj = DIRECT ? src.vel(e) : reinterpret_cast<const float4 *>(svel)[e];
-        const float rinv = rsqrtf(r2);
-        const float wgt = fmaf(-r2 * rinv, inv_rc, 1.f);
-        const float dot = dx * (vi4.x - vj.x) + dy * (vi4.y - vj.y) + dz * (vi4.z - vj.z);
-        const uint32_t word = dpd_word(tag_i, __float_as_int(vj.w), step, seed);
-        const float theta = 1.7320508075688772f * (2.f * unit_uniform(word) - 1.f);
-        const float fmag = c.A * wgt - c.gamma * wgt * wgt * dot * rinv + c.sigma_rdt * wgt * theta;
-        const float fr = fmag * rinv;
-        gx = fmaf(fr, dx, gx);
-        gy = fmaf(fr, dy, gy);
-        gz = fmaf(fr, dz, gz);
-        if (ENERGY) {
-          const float fx = fr * dx, fy = fr * dy, fz = fr * dz;
-          kpe.add(0.25f * c.A * r_cut_f * wgt * wgt);
-          kw[0].add(0.5f * dx * fx); kw[1].add(0.5f * dx * fy); kw[2].add(0.5f * dx * fz);
-          kw[3].add(0.5f * dy * fy); kw[4].add(0.5f * dy * fz); kw[5].add(0.5f * dz * fz);
-        }
-      }
-    }
-  };
   // the block's entries inside the FP32 band: decided in FP64 (rare)
   auto band_block = [&](const Word &w, float &gx, float &gy, float &gz) {
 #pragma unroll
@@ -605,13 +529,8 @@ __device__ __forceinline__ void pair_group(const KArgs &a, const BrickDesc &d, c
   auto two_blocks = [&](const Word &w0, const Word &w1, bool two) {
     if (MIXED) {
       float gx = 0.f, gy = 0.f, gz = 0.f, bmin = 3.0e38f;
-      if (POT == kDPD) {
-        dpd_block(w0, gx, gy, gz, bmin);
-        if (two) dpd_block(w1, gx, gy, gz, bmin);
-      } else {
-        mixed_block(w0, gx, gy, gz, bmin);
-        if (two) mixed_block(w1, gx, gy, gz, bmin);
-      }
+      mixed_block(w0, gx, gy, gz, bmin);
+      if (two) mixed_block(w1, gx, gy, gz, bmin);
       if (__any_sync(FULL, bmin <= bthr)) {
         band_block(w0, gx, gy, gz);
         if (two) band_block(w1, gx, gy, gz);
