@@ -215,6 +215,26 @@ struct MixedPair {
   }
 };
 
+// Half lists, Newton's third law: -f_ij on the partner j, and the other half
+// of the pair's energy and virial (d and f both change sign).  Out of line,
+// so that full-list kernels keep their own instruction schedule.
+template <bool ENERGY>
+static __device__ __noinline__ void partner_add(double *force, double *virial, int32_t j, double fx,
+                                                double fy, double fz, double v, double dx, double dy,
+                                                double dz) {
+  double *fj = force + 4 * (int64_t)j;
+  atomicAdd(fj + 0, -fx);
+  atomicAdd(fj + 1, -fy);
+  atomicAdd(fj + 2, -fz);
+  if (ENERGY) {
+    atomicAdd(fj + 3, 0.5 * v);
+    double *wj = virial + 6 * (int64_t)j;
+    atomicAdd(wj + 0, 0.5 * dx * fx); atomicAdd(wj + 1, 0.5 * dx * fy);
+    atomicAdd(wj + 2, 0.5 * dx * fz); atomicAdd(wj + 3, 0.5 * dy * fy);
+    atomicAdd(wj + 4, 0.5 * dy * fz); atomicAdd(wj + 5, 0.5 * dz * fz);
+  }
+}
+
 // Force on home particle i from the neighbour of entry e (FP64 path).
 template <int POT, bool ENERGY, bool ONE, bool DIRECT>
 struct DoublePair {
@@ -280,21 +300,9 @@ struct DoublePair {
       dw[0] += 0.5 * d[0] * fx; dw[1] += 0.5 * d[0] * fy; dw[2] += 0.5 * d[0] * fz;
       dw[3] += 0.5 * d[1] * fy; dw[4] += 0.5 * d[1] * fz; dw[5] += 0.5 * d[2] * fz;
     }
-    if (half) {
-      // Newton's third law: -f_ij on the partner, and the other half of the
-      // pair's energy and virial (d and f both change sign)
-      double *fj = reinterpret_cast<double *>(a.force) + 4 * (int64_t)j;
-      atomicAdd(fj + 0, -fx);
-      atomicAdd(fj + 1, -fy);
-      atomicAdd(fj + 2, -fz);
-      if (ENERGY) {
-        atomicAdd(fj + 3, 0.5 * v);
-        double *wj = reinterpret_cast<double *>(a.virial) + 6 * (int64_t)j;
-        atomicAdd(wj + 0, 0.5 * d[0] * fx); atomicAdd(wj + 1, 0.5 * d[0] * fy);
-        atomicAdd(wj + 2, 0.5 * d[0] * fz); atomicAdd(wj + 3, 0.5 * d[1] * fy);
-        atomicAdd(wj + 4, 0.5 * d[1] * fz); atomicAdd(wj + 5, 0.5 * d[2] * fz);
-      }
-    }
+    if (half)
+      partner_add<ENERGY>(reinterpret_cast<double *>(a.force), reinterpret_cast<double *>(a.virial), j,
+                          fx, fy, fz, v, d[0], d[1], d[2]);
   }
 };
 
