@@ -721,7 +721,9 @@ def main():
             for k in ("pos", "vel", "image", "tag", "type"):
                 setattr(st64, k, eq_state[k])
             g64 = graph_len(args.fp64_steps)
-            c64 = dict(common, thermo_period=g64, graph_steps=g64)
+            # the FP64 pair kernel reads each in-range neighbour's FP64 position
+            # from global memory: sorted at every rebuild, those reads stay local
+            c64 = dict(common, thermo_period=g64, graph_steps=g64, sort_period=1)
             s64 = md.MDSystem(st64, precision="fp64", stream=stream, max_nb=max_nb, **c64)
             for kern, name in ((md.KERNEL_PAIR, "pair"), (md.KERNEL_NLIST, "nlist")):
                 try:
