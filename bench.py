@@ -340,6 +340,22 @@ def pair_launch_ms(sysm, stream, torch, n_launch=30):
     return e0.elapsed_time(e1) / n_launch
 
 
+def nlist_build_ms(sysm, stream, torch, n_launch=5):
+    """Mean CUDA-event duration of back-to-back forced list builds on the
+    launching stream (the first, untimed call rebins the particles, so the
+    timed launches are the list kernel alone)."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sysm.build_nlist(True, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n_launch):
+        sysm.build_nlist(True, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n_launch
+
+
 def mean_neighbours(sysm, stream):
     counts, rows = sysm.nlist(stream)
     del rows
@@ -665,6 +681,7 @@ def main():
         # ---- pair-kernel roofline (CUDA events on the launching stream) ----
         nbar = mean_neighbours(sysm, stream)
         pair_ms = pair_launch_ms(sysm, stream, torch)
+        nlist_ms = nlist_build_ms(sysm, stream, torch)
         bytes_per_particle = 4.0 * nbar + 4 + 16 + 16 + 16
         achieved = args.n * bytes_per_particle / (pair_ms * 1e-3) / 1e9
         peak, peak_src = hbm_peak()
@@ -714,7 +731,8 @@ def main():
         launches = args.steps * (1 + 8 + 2 + 1 + 1) + 3 * (args.steps // g)
 
         forms = {"mixed": {"value": value, "ms_per_step": ms_per_step, "steps": args.steps,
-                           "graph_steps_used": g}}
+                           "graph_steps_used": g, "nlist_ms_per_build": nlist_ms,
+                           "builds": builds}}
         if want("fp64"):
             # plain FP64 path on the equilibrated state
             st64 = st.copy()

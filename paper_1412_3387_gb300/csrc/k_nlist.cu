@@ -37,20 +37,21 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// One pass: the brick's particles q0 .. q0 + 32 / WB - 1 (q0 a multiple of
+// the pair kernel's group size, so that a pass holds whole row groups).
 template <int WB, bool DIRECT>
 __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, const float4 *spos,
-                                           int j) {
-  constexpr int PB = 32 / WB;
+                                           int q0) {
   constexpr int U = 8;
   static_assert(U <= kStagePad, "a block of candidates may read U - 1 slots past a stage");
   const int lane = threadIdx.x & 31;
   const int qq = lane / WB, sl = lane & (WB - 1);
-  const int q = j * PB + qq;
+  const int q = q0 + qq;
   const bool active = q < d.nhome;
   const int qe = active ? qq : 0;
   const Rep &rp = a.rep[d.r];
   const bool ident = a.ident[d.r] != 0;
-  const HomeSlot hs = home_slot(d, j * PB + qe);
+  const HomeSlot hs = home_slot(d, q0 + qe);
   const int p = hs.p;
   const StageSrc<DIRECT> src{a, d, rp, smem_u32(spos), 0u};
   const float4 oi = src.pos((uint32_t)(hs.slot + 1));
@@ -67,7 +68,7 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
   const int lwp = a.w_store_log2, Wp = 1 << lwp, Pp = 32 >> lwp;
   const int Vp = row_depth(Wp);
   const int tcap = max_nb >> lwp;  // tiles a row region holds (a multiple of Vp)
-  const int gq = j * PB + qe;      // the particle's place in the brick
+  const int gq = q0 + qe;          // the particle's place in the brick
   const int grp = gq / Pp, q2 = gq - grp * Pp;
   const int pj = min(Pp, d.nhome - grp * Pp);
   uint16_t *gbase = a.nl + (size_t)(d.hstart + grp * Pp) * (size_t)max_nb;
@@ -309,11 +310,26 @@ __global__ void __launch_bounds__(kMaxBrickThreads, 1) k_nlist(KArgs a, int cap,
       if (k1 < kDescWords) dv1 = __ldg(src + k1);
     }
     const BrickDesc &d = M.desc(t);
-    const int ng = (d.nhome + PB - 1) / PB;
     if (d.off[64] > cap) {
-      for (int j = warp; j < ng; j += C) build_pass<WB, true>(a, d, M.pos(t), j);
+      for (int q0 = warp * PB; q0 < d.nhome; q0 += C * PB) build_pass<WB, true>(a, d, M.pos(t), q0);
     } else {
-      for (int j = warp; j < ng; j += C) build_pass<WB, false>(a, d, M.pos(t), j);
+      // whole rounds of one pass per warp; the rest, when it fits one round of
+      // passes at twice the lanes per particle (each lane then scans half a
+      // window), is split that way, so that the warps reach the brick barrier
+      // together instead of some waiting a whole pass for the others
+      const int whole = d.nhome / (C * PB) * (C * PB);
+      int q0 = warp * PB;
+      for (; q0 < whole; q0 += C * PB) build_pass<WB, false>(a, d, M.pos(t), q0);
+      if constexpr (WB < 32) {
+        constexpr int PH = PB / 2;
+        const int rest = d.nhome - whole;
+        if (2 * WB <= (1 << a.w_store_log2) && rest <= C * PH) {
+          const int qh = whole + warp * PH;
+          if (qh < d.nhome) build_pass<2 * WB, false>(a, d, M.pos(t), qh);
+          q0 = d.nhome;
+        }
+      }
+      for (; q0 < d.nhome; q0 += C * PB) build_pass<WB, false>(a, d, M.pos(t), q0);
     }
     if (has2) {
       uint4 *dst = reinterpret_cast<uint4 *>(&M.desc(t + 2));
