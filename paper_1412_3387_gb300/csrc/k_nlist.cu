@@ -11,8 +11,9 @@
 // by x, so each run is sorted by x at a build: the particle binary-searches
 // the part of each run within its reach in x (given its y-z distance to the
 // run's row of cells) and skips runs out of reach.  The W lanes of a particle
-// split that window into W contiguous parts.  After each block of U candidates the lanes of a
-// particle take an exclusive prefix sum of their hit counts and write their
+// split that window into W contiguous parts.  After each block of 32
+// candidates (screened in blocks of U = 8) the lanes of a particle take an
+// exclusive prefix sum of their hit counts and write their
 // hits straight into the row, in the pair kernel's tile layout (brick.cuh);
 // rows are then padded with the sentinel up to their group's tile count.
 // Rows thus come out compact and in a fixed, deterministic order (block by
