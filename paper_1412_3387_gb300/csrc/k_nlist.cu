@@ -73,8 +73,16 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
   const int grp = gq / Pp, q2 = gq - grp * Pp;
   const int pj = min(Pp, d.nhome - grp * Pp);
   uint16_t *gbase = a.nl + (size_t)(d.hstart + grp * Pp) * (size_t)max_nb;
+  // row_offset(k, lwp, pj, q2) with the particle's terms hoisted, in
+  // unsigned arithmetic (the terms joined by | occupy disjoint bits)
+  const unsigned lv = lwp <= 3 ? 2u : 5u - (unsigned)lwp;
+  const unsigned pjW = (unsigned)pj << lwp, qW = (unsigned)q2 << lwp;
+  auto offs = [&](unsigned k) -> unsigned {
+    const unsigned t = k >> lwp;
+    return ((((t >> lv) * pjW + qW) | (k & ((unsigned)Wp - 1u))) << lv) | (t & ((1u << lv) - 1u));
+  };
   auto put = [&](int k, uint16_t v) {
-    if ((k >> lwp) < tcap) gbase[row_offset(k, lwp, pj, q2)] = v;
+    if ((k >> lwp) < tcap) gbase[offs((unsigned)k)] = v;
   };
   // the nine runs of the particle's 3 x 3 x 3 stencil: stage cells
   // (hx .. hx + 2, hy + dy, hz + dz) for the home cell (hx + 1, hy + 1, hz + 1)
@@ -239,10 +247,19 @@ __device__ __forceinline__ void build_pass(const KArgs &a, const BrickDesc &d, c
       }
       const int tot = __shfl_sync(FULL, incl, lane | (WB - 1));
       int k = n + incl - h;
-      while (m) {
-        const int u = __ffs(m) - 1;
-        m &= m - 1u;
-        put(k++, (uint16_t)(beg + x0 + u + 1));
+      if (k + h <= (tcap << lwp)) {
+        // the common case: all of the lane's hits fit the row region
+        while (m) {
+          const int u = __ffs(m) - 1;
+          m &= m - 1u;
+          gbase[offs((unsigned)k++)] = (uint16_t)(beg + x0 + u + 1);
+        }
+      } else {
+        while (m) {
+          const int u = __ffs(m) - 1;
+          m &= m - 1u;
+          put(k++, (uint16_t)(beg + x0 + u + 1));
+        }
       }
       n += tot;
     }
