@@ -100,3 +100,26 @@ def test_null_handles_are_rejected(lib):
     assert lib.md_step(None, 0, None) == 1
     assert lib.md_poll_error(None, None) == 1
     assert lib.md_philox4x32_10(None, None, 5, None) == 1
+
+
+def test_workspace_size_checks_potential_arguments(lib):
+    """Host-side checks of the potentials' parameters: coefficient arrays must
+    be finite (3 per type pair for Morse), a tabulated pair needs 2 .. 65536
+    samples per type pair (and no coefficients), at most 64 angles per
+    particle, and a DPD temperature must be non-negative."""
+    morse = np.array([1.0, 2.0, 1.1])
+    p, keep = _params(pair=md.MORSE)
+    p.pair_coeff = morse.ctypes.data
+    assert _size(lib, p)[0] == md.MD_OK
+    bad = np.array([1.0, float("nan"), 1.1])
+    p.pair_coeff = bad.ctypes.data
+    assert _size(lib, p)[0] == 1
+    for pts, want in ((1, 1), (2, md.MD_OK), (65536, md.MD_OK), (65537, 1)):
+        p, keep = _params(pair=md.TABLE, table_points=pts)
+        p.pair_coeff = None
+        assert _size(lib, p)[0] == want, pts
+    for na, want in ((64, md.MD_OK), (65, 1), (-1, 1)):
+        p, keep = _params(max_angles=na)
+        assert _size(lib, p)[0] == want, na
+    p, keep = _params(pair=md.DPD, kT=-1.0)
+    assert _size(lib, p)[0] == 1
