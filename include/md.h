@@ -311,8 +311,11 @@ md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream st
  * first half step from the velocities at that time (call this again after
  * writing velocities directly).  Not valid with DPD pair forces (their
  * noise and friction are the thermostat).  Errors: MD_ERR_INVALID_ARG. */
-/* Half neighbour list with Newton's third law, FP64 forms only (Sec. 5.1
- * discusses full lists; the survey's "half list" row): with enable = 1 each
+md_status md_set_integrator(md_system *s, int32_t kind, double kT, double param,
+                            uint64_t seed);
+
+/* Half neighbour list with Newton's third law, FP64 forms only (not in the
+ * paper, whose Sec. 5.1 kernels use full lists): with enable = 1 each
  * pair within r_list is listed once, in the row of the particle with the
  * smaller cell-list position, and the pair kernel evaluates it once, adding
  * f_ij to that particle and -f_ij (and half the pair energy and virial) to
@@ -323,9 +326,6 @@ md_status md_run(md_system *s, int64_t n_steps, double *thermo_out, md_stream st
  * list is rebuilt at the next step.  Errors: MD_ERR_INVALID_ARG (enable not
  * 0 or 1, or a mixed-precision system). */
 md_status md_set_newton(md_system *s, int32_t enable);
-
-md_status md_set_integrator(md_system *s, int32_t kind, double kT, double param,
-                            uint64_t seed);
 
 /* Nose-Hoover state between steps (after the last completed step's end half
  * step), HOST [R][2] = (xi, eta) per replica.  Synchronises. */
